@@ -1,0 +1,210 @@
+/*
+ * pv.h -- C ABI of the GB300 primary-vertex library (libpvgb300.so).
+ *
+ * Primary-vertex finding and fitting for many independent bunch-crossing
+ * events, after Dziurda et al., "A parallel algorithm for fast reconstruction
+ * of primary vertices on heterogeneous architectures" (arXiv:2412.14966),
+ * Sec. 3.  Units: mm for positions, dimensionless slopes, mm^2 (and mm, 1) for
+ * covariance terms.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PV_OK (0) or one of the PV_ERR_* codes below; nothing is
+ *     thrown across the ABI.  pv_strerror() names a code.
+ *   - "device" pointers are CUDA device (or managed) memory on the context's
+ *     device; "host" pointers are ordinary or pinned host memory.  The caller
+ *     owns every input and output buffer; the context owns only its scratch
+ *     memory, CUDA graphs and serving state.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued asynchronously on it unless stated.
+ *   - Per-event and per-track problems are reported in the outputs (event and
+ *     vertex status words, track_vertex = -1), not as errors: a non-finite
+ *     track is simply not used.
+ */
+#ifndef PV_H
+#define PV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define PV_OK 0
+#define PV_ERR_ARG 1        /* invalid argument (NULL pointer, bad size, bad config) */
+#define PV_ERR_CUDA 2       /* a CUDA runtime call failed (see pv_last_cuda_error) */
+#define PV_ERR_CAPACITY 3   /* request larger than a fixed limit of the library */
+#define PV_ERR_NOMEM 4      /* scratch or serving pool could not be allocated / admitted */
+#define PV_ERR_TIMEOUT 5    /* a bounded wait ran out */
+#define PV_ERR_BUSY 6       /* serving queue full; retry after pv_poll */
+#define PV_ERR_NOTFOUND 7   /* unknown serving ticket */
+
+/* ---- vertex status bits (per fitted vertex) ---------------------------- */
+#define PV_ST_CONVERGED 1   /* x86 rule of Sec. 3.5: |dchi2| < tol and |dz| < tol */
+#define PV_ST_MAXITER 2     /* stopped at max_iter without converging */
+#define PV_ST_SINGULAR 4    /* normal matrix not positive definite (e.g. all weights 0) */
+#define PV_ST_REJ_BEAM 8    /* pp vertex farther than max_r_beam from the beamline */
+#define PV_ST_REJ_NTRK 16   /* fewer than min_pv_tracks tracks with weight > 0 */
+#define PV_ST_ACCEPTED 32   /* a primary vertex of the final selection (Sec. 3.5) */
+
+/* ---- event status bits -------------------------------------------------- */
+#define PV_EV_SEED_OVERFLOW 1  /* more seed clusters than the capacity; extra ones dropped */
+#define PV_EV_BAD_OFFSETS 4    /* offsets not monotone or outside [0, n_tracks]; not processed */
+
+/* ---- fixed limits -------------------------------------------------------- */
+#define PV_ONE 4096                   /* histogram weight of one track (fixed point) */
+#define PV_MAX_SEEDS 64               /* seed / vertex capacity per event */
+#define PV_MAX_BINS 4096              /* histogram bins per event */
+
+/* accumulation of the weighted normal equations in the fit */
+#define PV_ACCUM_FP32 0    /* binary32 per lane and across lanes */
+#define PV_ACCUM_KAHAN 1   /* compensated binary32 (error-free transformations) */
+
+/* execution path */
+#define PV_PATH_FUSED 0    /* bucketed persistent kernels, shared-memory histograms */
+#define PV_PATH_PLAIN 1    /* one kernel per step, global-memory histograms */
+
+/* Beamline at z = 0 and its slopes (Sec. 3: x_b, y_b, t_x,b, t_y,b). */
+typedef struct {
+  float x_b, y_b, tx_b, ty_b;
+} pv_beamline;
+
+/* Algorithm settings; pv_config_default() fills the paper's values. */
+typedef struct {
+  float z_min, z_max, dz;           /* histogram range and bin width (Sec. 3.2): -550, 300, 0.25 */
+  float z_gas;                      /* p-gas parameters below this z (Table smog-pp): -300 */
+  float sigma_max_pp, sigma_max_gas;        /* max sigma_poca to fill (Sec. 3.2): 1.5, 10 */
+  float min_integral_pp, min_integral_gas;  /* min cluster integral, tracks (Table smog-pp): 2.5, 1.75 */
+  uint32_t bin_threshold;           /* proto-cluster threshold in 1/PV_ONE tracks (unstated): 205 */
+  int32_t dip_num, dip_den;         /* dip significant if den*N_min < num*min(N_L, N_R) (unstated): 4, 5 */
+  int32_t min_assoc_pp, min_assoc_gas;      /* min tracks per cluster in association (Sec. 3.4): 3, 2 */
+  int32_t min_pv_tracks_pp, min_pv_tracks_gas;  /* min tracks with w > 0 (Table smog-pp): 4, 3 */
+  float chi2_max;                   /* Tukey cut-off (Sec. 3.5): 12 */
+  float dchi2_tol, dz_tol;          /* convergence (Sec. 3.5): 0.01, 0.001 mm */
+  int32_t max_iter;                 /* maximal fit iterations (Sec. 3.5): 10 */
+  float max_r_beam;                 /* final transverse cut for pp vertices (Sec. 3.5): 0.3 mm */
+  int32_t accum_mode;               /* PV_ACCUM_*: default PV_ACCUM_FP32 */
+  int32_t path;                     /* PV_PATH_*: default PV_PATH_FUSED */
+  uint64_t pool_bytes;              /* serving: device bytes admitted requests may pin (0 = 1 GiB) */
+  uint64_t max_spin_ns;             /* serving: bound of every wait (0 = 10 s) */
+} pv_config;
+
+/* Tracks in structure-of-arrays layout (Sec. 5, x86: one contiguous array per
+ * member), grouped by event through CSR offsets.  Track i of the batch has its
+ * state (x, y, t_x, t_y) at z (Sec. 2) and the covariance terms V_xx, V_xtx,
+ * V_txtx, V_yy, V_yty, V_tyty.  The 11 float arrays and event_offsets live in
+ * the same memory space (device for the device entry points, host for
+ * pv_run_host).  event_offsets has n_events + 1 entries; event e owns tracks
+ * [event_offsets[e], event_offsets[e+1]). */
+typedef struct {
+  const float *x, *y, *z, *tx, *ty;
+  const float *cxx, *cxtx, *ctxtx, *cyy, *cyty, *ctyty;
+  const int64_t* event_offsets;
+  int64_t n_tracks;
+  int32_t n_events;
+} pv_tracks;
+
+/* Seeds or vertices, row-major [event][capacity] unless stated.  Any pointer
+ * marked optional may be NULL.  cov holds 6 floats per vertex in the order
+ * xx, xy, yy, xz, yz, zz (C = (1/2 d2chi2/dalpha2)^-1, Sec. 3.5). */
+typedef struct {
+  float *x, *y, *z;             /* seed position (find) or fitted position (fit) */
+  float* cov;                   /* optional; [event][capacity][6] */
+  float *chi2, *ndof;           /* optional; vertex chi2 = chi2_0 + dchi2 and 2 sum(w) - 3 */
+  int32_t *n_tracks, *n_iter, *status;   /* optional; tracks with w > 0, iterations, PV_ST_* */
+  int32_t *bin_lo, *bin_hi, *bin_max;    /* optional; seed cluster bins and its maximum bin */
+  int32_t* n_per_event;         /* [n_events]: seeds (= vertices) of each event */
+  int32_t* event_status;        /* optional; [n_events] PV_EV_* bits */
+  int32_t* track_vertex;        /* [n_tracks]: seed / vertex index in its event, -1 if none */
+  int32_t capacity;             /* per event, 1 .. PV_MAX_SEEDS */
+} pv_vertices;
+
+typedef struct pv_ctx pv_ctx;
+
+/* Fill cfg with the paper's settings (values listed in pv_config). */
+void pv_config_default(pv_config* cfg);
+
+/* Create a context on CUDA device `device`.  cfg and beam are copied; NULL
+ * means defaults / a beamline at the origin with zero slope.  Checks the
+ * configuration (PV_ERR_ARG: nbins outside 1..PV_MAX_BINS, dz <= 0, ...).
+ * *out receives the context; release it with pv_destroy. */
+int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** out);
+
+/* Release the context, its scratch memory, graphs and serving state.  Waits
+ * (bounded by max_spin_ns) for in-flight serving requests. */
+int pv_destroy(pv_ctx* ctx);
+
+/* Steps (a)-(d1) of Sec. 3 on a batch: extrapolate each track to the
+ * beamline (Eq. zpocadef, sigma_poca of Sec. 3.1), fill each event's z
+ * histogram (Sec. 3.2), find seed clusters (Sec. 3.3) and associate tracks
+ * (Sec. 3.4).  tracks: device SoA.  seeds_out (device): x, y, z = seed
+ * position (beamline at z_seed); bin_lo/hi/max if given; n_per_event;
+ * event_status if given; track_vertex.  Asynchronous on cuda_stream.
+ * PV_ERR_ARG for NULL required pointers or capacity outside 1..64. */
+int pv_find_batch(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* seeds_out, void* cuda_stream);
+
+/* Steps (d2)-(d3): adaptive Tukey-weighted vertex fit of every seed from its
+ * associated tracks (Sec. 3.5) and the final selection.  seeds (device) as
+ * written by pv_find_batch (x, y, z, n_per_event, track_vertex are read);
+ * out (device) receives one vertex per seed, same indices, with status bits;
+ * out->n_per_event and out->track_vertex are written (copies of the seeds').
+ * seeds == NULL runs find and fit as one fused pass (the fast path).
+ * Asynchronous on cuda_stream. */
+int pv_fit_batch(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
+                 pv_vertices* out, void* cuda_stream);
+
+/* Step (a) alone: z_poca, sigma_poca and the center bin (-1 = not filled) of
+ * every track of the batch, in the pinned binary32 sequence.  Device
+ * outputs of n_tracks entries; any may be NULL.  Asynchronous. */
+int pv_extrapolate_batch(pv_ctx* ctx, const pv_tracks* tracks, float* zpoca, float* sigma_poca,
+                         int32_t* center_bin, void* cuda_stream);
+
+/* Steps (a)-(b): the integer histogram of every event (PV_ONE per fully
+ * contained track), row-major [n_events][nbins] uint32 in device memory.
+ * Asynchronous. */
+int pv_histogram_batch(pv_ctx* ctx, const pv_tracks* tracks, uint32_t* hist, void* cuda_stream);
+
+/* Number of histogram bins of the context's configuration. */
+int pv_num_bins(const pv_ctx* ctx);
+
+/* The whole method through host memory: copies the host SoA tracks to
+ * context-owned device buffers, runs the fused find+fit, copies the vertex
+ * outputs back into the host pv_vertices and synchronises cuda_stream.  All
+ * pointers in tracks and out are host pointers (pinned memory gives
+ * asynchronous copies).  Blocking. */
+int pv_run_host(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, void* cuda_stream);
+
+/* Serving.  pv_submit admits a request (device tracks and outputs, borrowed
+ * until pv_poll reports done) if the serving pool has room for it, and
+ * schedules it with other admitted requests; it never blocks.  *ticket
+ * identifies the request.  PV_ERR_BUSY if the queue is full,
+ * PV_ERR_NOMEM if the request alone exceeds pool_bytes. */
+int pv_submit(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, uint64_t* ticket);
+
+/* Non-blocking completion check: *done = 1 once the request's outputs are
+ * complete in device memory (and its latency recorded), else 0.
+ * PV_ERR_NOTFOUND for an unknown or already retired ticket. */
+int pv_poll(pv_ctx* ctx, uint64_t ticket, int* done);
+
+/* Latency of a completed request in nanoseconds, from pv_submit to the moment
+ * the stream reached the end of its work, then retires the ticket (later
+ * calls with it return PV_ERR_NOTFOUND).  PV_ERR_NOTFOUND if the ticket is
+ * unknown or not yet done. */
+int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns);
+
+/* Human-readable name of an error code. */
+const char* pv_strerror(int code);
+
+/* The last CUDA error string seen by the context (or "" if none). */
+const char* pv_last_cuda_error(const pv_ctx* ctx);
+
+/* Number of kernel launches the library enqueued since the context was
+ * created (all entry points); used to count launches in a timed region. */
+uint64_t pv_launch_count(const pv_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PV_H */

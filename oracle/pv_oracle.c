@@ -32,6 +32,8 @@
  *   R8 final track count = tracks with w > 0 in the last iteration.
  *   R9 seed position: delta and z_seed in binary64 from the exact integer bin
  *      contents, rounded once to binary32; delta = 0 when 2N_i - N_+ - N_- <= 0.
+ *   R10 the fit uses a track only if its state is finite and both variances
+ *      extrapolated to the seed z are finite and positive.
  */
 #include <math.h>
 #include <stdint.h>
@@ -508,7 +510,7 @@ static void oc_fit_track_from(const float* const* T, int64_t t, double zs, oc_fi
   double vyy = (double)T[8][t] + 2.0 * d * (double)T[9][t] + d * d * (double)T[10][t];
   f->wx = 1.0 / vxx;
   f->wy = 1.0 / vyy;
-  f->usable = (vxx > 0.0) && (vyy > 0.0) && isfinite(f->wx) && isfinite(f->wy) &&
+  f->usable = (vxx > 0.0) && (vyy > 0.0) && isfinite(vxx) && isfinite(vyy) &&
               isfinite(f->x) && isfinite(f->y) && isfinite(f->z) &&
               isfinite(f->tx) && isfinite(f->ty);
 }

@@ -1,0 +1,744 @@
+// pv_api.cu -- the C ABI declared in include/pv.h.
+//
+// Host side only: argument checks, context-owned scratch, dispatch to the
+// fused or the plain kernels, the host-buffer entry point, and the serving
+// layer (continuous batching over several CUDA streams with admission by a
+// device memory pool).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pv.h"
+#include "pv_kernels.cuh"
+
+using pvdev::Consts;
+
+namespace {
+
+uint64_t now_ns() {
+  return static_cast<uint64_t>(std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                   std::chrono::steady_clock::now().time_since_epoch())
+                                   .count());
+}
+
+// A device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t want = need + need / 4 + 4096;
+    cudaError_t err = cudaMalloc(&p, want);
+    if (err != cudaSuccess) { p = nullptr; return err; }
+    bytes = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+size_t round16(size_t v) { return (v + 15) / 16 * 16; }
+
+// Carves fused-path scratch for n_tracks tracks out of one buffer.
+struct FusedLayout {
+  size_t counter, center, cid, slot, A, W, total;
+  explicit FusedLayout(int64_t n) {
+    size_t o = 0;
+    counter = o; o += 256;
+    A = o; o += round16(sizeof(float4) * n);
+    W = o; o += round16(sizeof(float2) * n);
+    center = o; o += round16(sizeof(int32_t) * n);
+    cid = o; o += round16(sizeof(int32_t) * n);
+    slot = o; o += round16(sizeof(int32_t) * n);
+    total = o;
+  }
+  pvk::TrackScratch scratch(void* base) const {
+    char* b = static_cast<char*>(base);
+    pvk::TrackScratch s;
+    s.center = reinterpret_cast<int32_t*>(b + center);
+    s.cid = reinterpret_cast<int32_t*>(b + cid);
+    s.slot = reinterpret_cast<int32_t*>(b + slot);
+    s.A = reinterpret_cast<float4*>(b + A);
+    s.W = reinterpret_cast<float2*>(b + W);
+    return s;
+  }
+  int* work_counter(void* base) const {
+    return reinterpret_cast<int*>(static_cast<char*>(base) + counter);
+  }
+};
+
+struct PlainLayout {
+  size_t zpoca, sigma, center, j0, j1, hist, seed_n, seed_lo, seed_hi, seed_bin, seed_z, cid,
+      slot, A, W, ev, total;
+  PlainLayout(int64_t n, int64_t E, int nbins) {
+    size_t o = 0;
+    A = o; o += round16(sizeof(float4) * n);
+    W = o; o += round16(sizeof(float2) * n);
+    zpoca = o; o += round16(4 * n);
+    sigma = o; o += round16(4 * n);
+    center = o; o += round16(4 * n);
+    j0 = o; o += round16(4 * n);
+    j1 = o; o += round16(4 * n);
+    cid = o; o += round16(4 * n);
+    slot = o; o += round16(4 * n);
+    hist = o; o += round16(4 * static_cast<size_t>(E) * nbins);
+    seed_n = o; o += round16(4 * E);
+    ev = o; o += round16(4 * E);
+    seed_lo = o; o += round16(4 * E * PV_MAX_SEEDS);
+    seed_hi = o; o += round16(4 * E * PV_MAX_SEEDS);
+    seed_bin = o; o += round16(4 * E * PV_MAX_SEEDS);
+    seed_z = o; o += round16(4 * E * PV_MAX_SEEDS);
+    total = o;
+  }
+  pvk::PlainScratch scratch(void* base) const {
+    char* b = static_cast<char*>(base);
+    pvk::PlainScratch s;
+    s.zpoca = reinterpret_cast<float*>(b + zpoca);
+    s.sigma = reinterpret_cast<float*>(b + sigma);
+    s.center = reinterpret_cast<int32_t*>(b + center);
+    s.j0 = reinterpret_cast<int32_t*>(b + j0);
+    s.j1 = reinterpret_cast<int32_t*>(b + j1);
+    s.hist = reinterpret_cast<uint32_t*>(b + hist);
+    s.seed_n = reinterpret_cast<int32_t*>(b + seed_n);
+    s.seed_lo = reinterpret_cast<int32_t*>(b + seed_lo);
+    s.seed_hi = reinterpret_cast<int32_t*>(b + seed_hi);
+    s.seed_bin = reinterpret_cast<int32_t*>(b + seed_bin);
+    s.seed_z = reinterpret_cast<float*>(b + seed_z);
+    s.cid = reinterpret_cast<int32_t*>(b + cid);
+    s.slot = reinterpret_cast<int32_t*>(b + slot);
+    s.A = reinterpret_cast<float4*>(b + A);
+    s.W = reinterpret_cast<float2*>(b + W);
+    s.ev_status = reinterpret_cast<int32_t*>(b + ev);
+    return s;
+  }
+};
+
+// ---- serving --------------------------------------------------------------
+
+constexpr int kServeStreams = 4;
+constexpr size_t kMaxQueued = 4096;
+
+struct Request {
+  uint64_t ticket = 0;
+  pv_tracks tracks{};
+  pv_vertices out{};
+  size_t bytes = 0;
+  size_t arena_off = 0;
+  uint64_t t_submit = 0;
+  std::atomic<uint64_t> t_done{0};
+  std::atomic<int> done{0};
+  bool admitted = false;
+  int stream = 0;
+};
+
+// First-fit allocator over [0, size) with out-of-order frees.
+struct Arena {
+  size_t size = 0;
+  std::map<size_t, size_t> free_;   // offset -> length
+  void reset(size_t s) {
+    size = s;
+    free_.clear();
+    free_[0] = s;
+  }
+  bool alloc(size_t n, size_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        size_t rest = it->second - n;
+        size_t start = it->first + n;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+}  // namespace
+
+struct pv_ctx {
+  int device = 0;
+  pv_config cfg{};
+  pv_beamline beam{};
+  Consts C{};
+  int n_sm = 0;
+  int fused_grid[4] = {0, 0, 0, 0};   // by mode
+  DevBuf fused_ws, plain_ws;
+  // host-buffer entry point staging
+  DevBuf host_in, host_out;
+  cudaStream_t own_stream = nullptr;
+  std::atomic<uint64_t> launches{0};
+  std::string last_error;
+  // serving
+  std::mutex mu;
+  DevBuf pool;
+  Arena arena;
+  bool pool_ready = false;
+  cudaStream_t serve_streams[kServeStreams] = {};
+  int next_stream = 0;
+  uint64_t next_ticket = 1;
+  std::deque<Request*> pending;
+  std::unordered_map<uint64_t, Request*> requests;
+  std::deque<uint64_t> retired_order;
+};
+
+namespace {
+
+int fail_cuda(pv_ctx* ctx, cudaError_t err) {
+  if (ctx) ctx->last_error = cudaGetErrorString(err);
+  return PV_ERR_CUDA;
+}
+
+#define PV_CUDA(ctx, call)                              \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return fail_cuda(ctx, _e);   \
+  } while (0)
+
+int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
+  if (!(cfg.dz > 0.0f) || !(cfg.z_max > cfg.z_min)) return PV_ERR_ARG;
+  double nb = std::floor((static_cast<double>(cfg.z_max) - static_cast<double>(cfg.z_min)) /
+                             static_cast<double>(cfg.dz) + 0.5);
+  if (!(nb >= 1.0) || nb > PV_MAX_BINS) return PV_ERR_ARG;
+  if (cfg.dip_den <= 0 || cfg.dip_num < 0) return PV_ERR_ARG;
+  if (!(cfg.chi2_max > 0.0f) || cfg.max_iter < 0 || cfg.max_iter > 1000) return PV_ERR_ARG;
+  if (cfg.accum_mode != PV_ACCUM_FP32 && cfg.accum_mode != PV_ACCUM_KAHAN) return PV_ERR_ARG;
+  if (cfg.path != PV_PATH_FUSED && cfg.path != PV_PATH_PLAIN) return PV_ERR_ARG;
+  if (!(cfg.min_integral_pp >= 0.0f) || !(cfg.min_integral_gas >= 0.0f)) return PV_ERR_ARG;
+  C->z_min = cfg.z_min;
+  C->dz = cfg.dz;
+  C->z_gas = cfg.z_gas;
+  C->sig_max_pp = cfg.sigma_max_pp;
+  C->sig_max_gas = cfg.sigma_max_gas;
+  C->x_b = b.x_b;
+  C->y_b = b.y_b;
+  C->tx_b = b.tx_b;
+  C->ty_b = b.ty_b;
+  C->chi2_max = cfg.chi2_max;
+  C->inv_chi2_max = 1.0f / cfg.chi2_max;
+  C->dchi2_tol = cfg.dchi2_tol;
+  C->dz_tol = cfg.dz_tol;
+  C->max_r_beam = cfg.max_r_beam;
+  C->thr = cfg.bin_threshold;
+  C->t_pp = static_cast<uint32_t>(std::llround(static_cast<double>(cfg.min_integral_pp) * PV_ONE));
+  C->t_gas = static_cast<uint32_t>(std::llround(static_cast<double>(cfg.min_integral_gas) * PV_ONE));
+  C->dip_num = cfg.dip_num;
+  C->dip_den = cfg.dip_den;
+  C->min_assoc_pp = cfg.min_assoc_pp;
+  C->min_assoc_gas = cfg.min_assoc_gas;
+  C->min_pv_pp = cfg.min_pv_tracks_pp;
+  C->min_pv_gas = cfg.min_pv_tracks_gas;
+  C->nbins = static_cast<int>(nb);
+  C->ntiles = (C->nbins + 31) / 32;
+  // bin of z_gas by the same binary32 rule as the kernels
+  volatile float diff = cfg.z_gas - cfg.z_min;
+  volatile float q = diff / cfg.dz;
+  int gb;
+  if (!(q >= 0.0f)) gb = -1;
+  else if (q >= static_cast<float>(C->nbins)) gb = C->nbins;
+  else gb = static_cast<int>(q);
+  C->gas_bin = gb;
+  C->max_iter = cfg.max_iter;
+  C->accum_mode = cfg.accum_mode;
+  return PV_OK;
+}
+
+int check_tracks(const pv_tracks* t) {
+  if (!t) return PV_ERR_ARG;
+  if (t->n_events < 0 || t->n_tracks < 0) return PV_ERR_ARG;
+  if (t->n_events > 0 && !t->event_offsets) return PV_ERR_ARG;
+  if (t->n_tracks > 0) {
+    const float* p[11] = {t->x, t->y, t->z, t->tx, t->ty, t->cxx, t->cxtx, t->ctxtx,
+                          t->cyy, t->cyty, t->ctyty};
+    for (auto q : p)
+      if (!q) return PV_ERR_ARG;
+  }
+  return PV_OK;
+}
+
+int check_out(const pv_vertices* o, int64_t n_tracks, bool need_xyz) {
+  if (!o) return PV_ERR_ARG;
+  if (o->capacity < 1 || o->capacity > PV_MAX_SEEDS) return PV_ERR_ARG;
+  if (!o->n_per_event) return PV_ERR_ARG;
+  if (n_tracks > 0 && !o->track_vertex) return PV_ERR_ARG;
+  if (need_xyz && (!o->x || !o->y || !o->z)) return PV_ERR_ARG;
+  return PV_OK;
+}
+
+pvk::TrackPtrs track_ptrs(const pv_tracks* t) {
+  pvk::TrackPtrs T;
+  T.x = t->x; T.y = t->y; T.z = t->z; T.tx = t->tx; T.ty = t->ty;
+  T.cxx = t->cxx; T.cxtx = t->cxtx; T.ctxtx = t->ctxtx;
+  T.cyy = t->cyy; T.cyty = t->cyty; T.ctyty = t->ctyty;
+  T.off = t->event_offsets;
+  T.n_tracks = t->n_tracks;
+  T.n_events = t->n_events;
+  return T;
+}
+
+pvk::OutPtrs out_ptrs(const pv_vertices* o) {
+  pvk::OutPtrs O;
+  O.x = o->x; O.y = o->y; O.z = o->z; O.cov = o->cov; O.chi2 = o->chi2; O.ndof = o->ndof;
+  O.n_tracks = o->n_tracks; O.n_iter = o->n_iter; O.status = o->status;
+  O.bin_lo = o->bin_lo; O.bin_hi = o->bin_hi; O.bin_max = o->bin_max;
+  O.n_per_event = o->n_per_event; O.event_status = o->event_status;
+  O.track_vertex = o->track_vertex;
+  O.cap = o->capacity;
+  return O;
+}
+
+pvk::SeedPtrs seed_ptrs(const pv_vertices* s) {
+  pvk::SeedPtrs S{};
+  if (!s) return S;
+  S.x = s->x; S.y = s->y; S.z = s->z;
+  S.n_per_event = s->n_per_event;
+  S.track_vertex = s->track_vertex;
+  S.cap = s->capacity;
+  return S;
+}
+
+// Enqueue the fused kernel with scratch at `base` (laid out by FusedLayout).
+int enqueue_fused(pv_ctx* ctx, int mode, const pv_tracks* tracks, const pv_vertices* seeds,
+                  const pv_vertices* out, void* base, cudaStream_t st) {
+  FusedLayout L(tracks->n_tracks);
+  int grid = ctx->fused_grid[mode];
+  if (grid < 1) grid = ctx->n_sm;
+  PV_CUDA(ctx, pvk::launch_fused(mode, ctx->C, track_ptrs(tracks), seed_ptrs(seeds),
+                                 out_ptrs(out), L.scratch(base), L.work_counter(base), grid, st));
+  ctx->launches += 1;
+  return PV_OK;
+}
+
+int run_find_or_fit(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
+                    pv_vertices* out, cudaStream_t st, int mode) {
+  if (tracks->n_events == 0) return PV_OK;
+  if (ctx->cfg.path == PV_PATH_PLAIN) {
+    PlainLayout L(tracks->n_tracks, tracks->n_events, ctx->C.nbins);
+    PV_CUDA(ctx, ctx->plain_ws.ensure(L.total));
+    pvk::PlainScratch ws = L.scratch(ctx->plain_ws.p);
+    int n = 0;
+    pvk::TrackPtrs T = track_ptrs(tracks);
+    if (mode & pvk::kFind) {
+      PV_CUDA(ctx, pvk::launch_plain_find(ctx->C, T, out_ptrs(out), ws, st, &n));
+    }
+    if (mode & pvk::kFit) {
+      const pv_vertices* src = (mode & pvk::kFind) ? out : seeds;
+      PV_CUDA(ctx, pvk::launch_plain_fit(ctx->C, T, seed_ptrs(src), out_ptrs(out), ws, st, &n));
+    }
+    ctx->launches += n;
+    return PV_OK;
+  }
+  FusedLayout L(tracks->n_tracks);
+  PV_CUDA(ctx, ctx->fused_ws.ensure(L.total));
+  return enqueue_fused(ctx, mode, tracks, seeds, out, ctx->fused_ws.p, st);
+}
+
+// ---- serving internals (ctx->mu held) ------------------------------------
+
+size_t request_bytes(const pv_tracks* t) { return FusedLayout(t->n_tracks).total; }
+
+void CUDART_CB on_request_done(void* arg) {
+  Request* r = static_cast<Request*>(arg);
+  r->t_done.store(now_ns());
+  r->done.store(1);
+}
+
+int ensure_pool(pv_ctx* ctx) {
+  if (ctx->pool_ready) return PV_OK;
+  size_t bytes = ctx->cfg.pool_bytes ? ctx->cfg.pool_bytes : (size_t(1) << 30);
+  PV_CUDA(ctx, ctx->pool.ensure(bytes));
+  ctx->arena.reset(ctx->pool.bytes / 256 * 256);
+  for (int i = 0; i < kServeStreams; ++i)
+    PV_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->serve_streams[i], cudaStreamNonBlocking));
+  ctx->pool_ready = true;
+  return PV_OK;
+}
+
+// Launch a request on a serving stream with scratch from the arena.
+int launch_request(pv_ctx* ctx, Request* r) {
+  cudaStream_t st = ctx->serve_streams[r->stream];
+  char* base = static_cast<char*>(ctx->pool.p) + r->arena_off;
+  int rc = enqueue_fused(ctx, pvk::kFindFit, &r->tracks, nullptr, &r->out, base, st);
+  if (rc != PV_OK) return rc;
+  PV_CUDA(ctx, cudaLaunchHostFunc(st, on_request_done, r));
+  return PV_OK;
+}
+
+// Retire completed requests' memory and admit pending ones that now fit.
+int pump(pv_ctx* ctx) {
+  for (auto& kv : ctx->requests) {
+    Request* r = kv.second;
+    if (r->admitted && r->done.load() && r->bytes) {
+      ctx->arena.release(r->arena_off, r->bytes);
+      r->bytes = 0;
+    }
+  }
+  while (!ctx->pending.empty()) {
+    Request* r = ctx->pending.front();
+    size_t off;
+    if (!ctx->arena.alloc(r->bytes, &off)) break;
+    r->arena_off = off;
+    r->admitted = true;
+    r->stream = ctx->next_stream;
+    ctx->next_stream = (ctx->next_stream + 1) % kServeStreams;
+    ctx->pending.pop_front();
+    int rc = launch_request(ctx, r);
+    if (rc != PV_OK) return rc;
+  }
+  return PV_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+void pv_config_default(pv_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->z_min = -550.0f;
+  c->z_max = 300.0f;
+  c->dz = 0.25f;
+  c->z_gas = -300.0f;
+  c->sigma_max_pp = 1.5f;
+  c->sigma_max_gas = 10.0f;
+  c->min_integral_pp = 2.5f;
+  c->min_integral_gas = 1.75f;
+  c->bin_threshold = 205;
+  c->dip_num = 4;
+  c->dip_den = 5;
+  c->min_assoc_pp = 3;
+  c->min_assoc_gas = 2;
+  c->min_pv_tracks_pp = 4;
+  c->min_pv_tracks_gas = 3;
+  c->chi2_max = 12.0f;
+  c->dchi2_tol = 0.01f;
+  c->dz_tol = 0.001f;
+  c->max_iter = 10;
+  c->max_r_beam = 0.3f;
+  c->accum_mode = PV_ACCUM_FP32;
+  c->path = PV_PATH_FUSED;
+  c->pool_bytes = 0;
+  c->max_spin_ns = 0;
+}
+
+int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** out) {
+  if (!out) return PV_ERR_ARG;
+  *out = nullptr;
+  pv_config c;
+  if (cfg) c = *cfg; else pv_config_default(&c);
+  pv_beamline b{0.f, 0.f, 0.f, 0.f};
+  if (beam) b = *beam;
+  Consts C;
+  int rc = compute_consts(c, b, &C);
+  if (rc != PV_OK) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return PV_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return PV_ERR_CUDA;
+  pv_ctx* ctx = new (std::nothrow) pv_ctx();
+  if (!ctx) return PV_ERR_NOMEM;
+  ctx->device = device;
+  ctx->cfg = c;
+  ctx->beam = b;
+  ctx->C = C;
+  if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      pvk::fused_setup(C.nbins) != cudaSuccess) {
+    delete ctx;
+    return PV_ERR_CUDA;
+  }
+  for (int mode = 1; mode <= 3; ++mode) {
+    int per_sm = pvk::fused_blocks_per_sm(C.nbins, mode);
+    ctx->fused_grid[mode] = ctx->n_sm * (per_sm > 0 ? per_sm : 1);
+  }
+  *out = ctx;
+  return PV_OK;
+}
+
+int pv_destroy(pv_ctx* ctx) {
+  if (!ctx) return PV_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  int rc = PV_OK;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    uint64_t limit = ctx->cfg.max_spin_ns ? ctx->cfg.max_spin_ns : 10000000000ull;
+    uint64_t t0 = now_ns();
+    // bounded wait for admitted requests; pending ones are dropped
+    for (;;) {
+      bool busy = false;
+      for (auto& kv : ctx->requests)
+        if (kv.second->admitted && !kv.second->done.load()) busy = true;
+      if (!busy) break;
+      if (now_ns() - t0 > limit) { rc = PV_ERR_TIMEOUT; break; }
+      std::this_thread::yield();
+    }
+    if (rc == PV_OK) {
+      for (auto& kv : ctx->requests) delete kv.second;
+      ctx->requests.clear();
+      for (int i = 0; i < kServeStreams; ++i)
+        if (ctx->serve_streams[i]) cudaStreamDestroy(ctx->serve_streams[i]);
+    }
+  }
+  if (rc != PV_OK) return rc;   // leave the context alive: its requests still run
+  cudaDeviceSynchronize();
+  ctx->fused_ws.release();
+  ctx->plain_ws.release();
+  ctx->host_in.release();
+  ctx->host_out.release();
+  ctx->pool.release();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+  return PV_OK;
+}
+
+int pv_num_bins(const pv_ctx* ctx) { return ctx ? ctx->C.nbins : 0; }
+
+int pv_find_batch(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* seeds_out, void* stream) {
+  if (!ctx) return PV_ERR_ARG;
+  int rc = check_tracks(tracks);
+  if (rc != PV_OK) return rc;
+  rc = check_out(seeds_out, tracks->n_tracks, true);
+  if (rc != PV_OK) return rc;
+  cudaSetDevice(ctx->device);
+  return run_find_or_fit(ctx, tracks, nullptr, seeds_out, static_cast<cudaStream_t>(stream),
+                         pvk::kFind);
+}
+
+int pv_fit_batch(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds, pv_vertices* out,
+                 void* stream) {
+  if (!ctx) return PV_ERR_ARG;
+  int rc = check_tracks(tracks);
+  if (rc != PV_OK) return rc;
+  rc = check_out(out, tracks->n_tracks, true);
+  if (rc != PV_OK) return rc;
+  if (seeds) {
+    rc = check_out(seeds, tracks->n_tracks, true);
+    if (rc != PV_OK) return rc;
+  }
+  cudaSetDevice(ctx->device);
+  return run_find_or_fit(ctx, tracks, seeds, out, static_cast<cudaStream_t>(stream),
+                         seeds ? pvk::kFit : pvk::kFindFit);
+}
+
+int pv_extrapolate_batch(pv_ctx* ctx, const pv_tracks* tracks, float* zpoca, float* sigma,
+                         int32_t* center, void* stream) {
+  if (!ctx) return PV_ERR_ARG;
+  int rc = check_tracks(tracks);
+  if (rc != PV_OK) return rc;
+  cudaSetDevice(ctx->device);
+  if (tracks->n_tracks == 0) return PV_OK;
+  PV_CUDA(ctx, pvk::launch_extrapolate(ctx->C, track_ptrs(tracks), zpoca, sigma, center,
+                                       static_cast<cudaStream_t>(stream)));
+  ctx->launches += 1;
+  return PV_OK;
+}
+
+int pv_histogram_batch(pv_ctx* ctx, const pv_tracks* tracks, uint32_t* hist, void* stream) {
+  if (!ctx || !hist) return PV_ERR_ARG;
+  int rc = check_tracks(tracks);
+  if (rc != PV_OK) return rc;
+  cudaSetDevice(ctx->device);
+  if (tracks->n_events == 0) return PV_OK;
+  PlainLayout L(tracks->n_tracks, 0, ctx->C.nbins);
+  PV_CUDA(ctx, ctx->plain_ws.ensure(L.total));
+  int n = 0;
+  PV_CUDA(ctx, pvk::launch_histogram(ctx->C, track_ptrs(tracks), hist, L.scratch(ctx->plain_ws.p),
+                                     static_cast<cudaStream_t>(stream), &n));
+  ctx->launches += n;
+  return PV_OK;
+}
+
+int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) {
+  if (!ctx) return PV_ERR_ARG;
+  int rc = check_tracks(h);
+  if (rc != PV_OK) return rc;
+  rc = check_out(ho, h->n_tracks, true);
+  if (rc != PV_OK) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = h->n_tracks;
+  const int64_t E = h->n_events;
+  const size_t cap = static_cast<size_t>(ho->capacity);
+  // device inputs: 11 float arrays + offsets
+  size_t in_bytes = 11 * round16(4 * n) + round16(8 * (E + 1));
+  PV_CUDA(ctx, ctx->host_in.ensure(in_bytes));
+  char* din = static_cast<char*>(ctx->host_in.p);
+  const float* src[11] = {h->x, h->y, h->z, h->tx, h->ty, h->cxx, h->cxtx, h->ctxtx,
+                          h->cyy, h->cyty, h->ctyty};
+  float* dcol[11];
+  for (int k = 0; k < 11; ++k) {
+    dcol[k] = reinterpret_cast<float*>(din + k * round16(4 * n));
+    if (n) PV_CUDA(ctx, cudaMemcpyAsync(dcol[k], src[k], 4 * n, cudaMemcpyHostToDevice, st));
+  }
+  int64_t* doff = reinterpret_cast<int64_t*>(din + 11 * round16(4 * n));
+  if (E) PV_CUDA(ctx, cudaMemcpyAsync(doff, h->event_offsets, 8 * (E + 1), cudaMemcpyHostToDevice, st));
+  pv_tracks dt = *h;
+  dt.x = dcol[0]; dt.y = dcol[1]; dt.z = dcol[2]; dt.tx = dcol[3]; dt.ty = dcol[4];
+  dt.cxx = dcol[5]; dt.cxtx = dcol[6]; dt.ctxtx = dcol[7];
+  dt.cyy = dcol[8]; dt.cyty = dcol[9]; dt.ctyty = dcol[10];
+  dt.event_offsets = doff;
+  // device outputs mirror the non-NULL host outputs
+  const size_t nv = static_cast<size_t>(E) * cap;
+  struct Col { void* host; size_t bytes; } cols[16];
+  int nc = 0;
+  size_t o = 0;
+  auto plan = [&](void* hp, size_t bytes) -> size_t {
+    size_t off = o;
+    if (hp) { cols[nc++] = {hp, bytes}; o += round16(bytes); }
+    return off;
+  };
+  size_t ox = plan(ho->x, 4 * nv), oy = plan(ho->y, 4 * nv), oz = plan(ho->z, 4 * nv);
+  size_t ocov = plan(ho->cov, 24 * nv), ochi = plan(ho->chi2, 4 * nv), ondf = plan(ho->ndof, 4 * nv);
+  size_t ontr = plan(ho->n_tracks, 4 * nv), onit = plan(ho->n_iter, 4 * nv);
+  size_t ost = plan(ho->status, 4 * nv), olo = plan(ho->bin_lo, 4 * nv);
+  size_t ohi = plan(ho->bin_hi, 4 * nv), obm = plan(ho->bin_max, 4 * nv);
+  size_t onpe = plan(ho->n_per_event, 4 * E), oevs = plan(ho->event_status, 4 * E);
+  size_t otv = plan(ho->track_vertex, 4 * n);
+  PV_CUDA(ctx, ctx->host_out.ensure(o + 16));
+  char* dout = static_cast<char*>(ctx->host_out.p);
+  pv_vertices dv = *ho;
+  auto dp = [&](void* hp, size_t off) -> void* { return hp ? dout + off : nullptr; };
+  dv.x = static_cast<float*>(dp(ho->x, ox));
+  dv.y = static_cast<float*>(dp(ho->y, oy));
+  dv.z = static_cast<float*>(dp(ho->z, oz));
+  dv.cov = static_cast<float*>(dp(ho->cov, ocov));
+  dv.chi2 = static_cast<float*>(dp(ho->chi2, ochi));
+  dv.ndof = static_cast<float*>(dp(ho->ndof, ondf));
+  dv.n_tracks = static_cast<int32_t*>(dp(ho->n_tracks, ontr));
+  dv.n_iter = static_cast<int32_t*>(dp(ho->n_iter, onit));
+  dv.status = static_cast<int32_t*>(dp(ho->status, ost));
+  dv.bin_lo = static_cast<int32_t*>(dp(ho->bin_lo, olo));
+  dv.bin_hi = static_cast<int32_t*>(dp(ho->bin_hi, ohi));
+  dv.bin_max = static_cast<int32_t*>(dp(ho->bin_max, obm));
+  dv.n_per_event = static_cast<int32_t*>(dp(ho->n_per_event, onpe));
+  dv.event_status = static_cast<int32_t*>(dp(ho->event_status, oevs));
+  dv.track_vertex = static_cast<int32_t*>(dp(ho->track_vertex, otv));
+  rc = run_find_or_fit(ctx, &dt, nullptr, &dv, st, pvk::kFindFit);
+  if (rc != PV_OK) return rc;
+  size_t off = 0;
+  for (int k = 0; k < nc; ++k) {
+    if (cols[k].bytes)
+      PV_CUDA(ctx, cudaMemcpyAsync(cols[k].host, dout + off, cols[k].bytes, cudaMemcpyDeviceToHost, st));
+    off += round16(cols[k].bytes);
+  }
+  PV_CUDA(ctx, cudaStreamSynchronize(st));
+  return PV_OK;
+}
+
+int pv_submit(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, uint64_t* ticket) {
+  if (!ctx || !ticket) return PV_ERR_ARG;
+  int rc = check_tracks(tracks);
+  if (rc != PV_OK) return rc;
+  rc = check_out(out, tracks->n_tracks, true);
+  if (rc != PV_OK) return rc;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  rc = ensure_pool(ctx);
+  if (rc != PV_OK) return rc;
+  size_t bytes = (request_bytes(tracks) + 255) / 256 * 256;
+  if (bytes > ctx->arena.size) return PV_ERR_NOMEM;
+  if (ctx->pending.size() >= kMaxQueued) {
+    rc = pump(ctx);
+    if (rc != PV_OK) return rc;
+    if (ctx->pending.size() >= kMaxQueued) return PV_ERR_BUSY;
+  }
+  Request* r = new (std::nothrow) Request();
+  if (!r) return PV_ERR_NOMEM;
+  r->ticket = ctx->next_ticket++;
+  r->tracks = *tracks;
+  r->out = *out;
+  r->bytes = bytes;
+  r->t_submit = now_ns();
+  if (tracks->n_events == 0) {
+    r->done.store(1);
+    r->t_done.store(r->t_submit);
+    r->admitted = true;
+    r->bytes = 0;
+  } else {
+    ctx->pending.push_back(r);
+  }
+  ctx->requests[r->ticket] = r;
+  *ticket = r->ticket;
+  return pump(ctx);
+}
+
+int pv_poll(pv_ctx* ctx, uint64_t ticket, int* done) {
+  if (!ctx || !done) return PV_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->requests.find(ticket);
+  if (it == ctx->requests.end()) return PV_ERR_NOTFOUND;
+  int rc = pump(ctx);
+  *done = it->second->done.load();
+  return rc;
+}
+
+int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns) {
+  if (!ctx || !ns) return PV_ERR_ARG;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->requests.find(ticket);
+  if (it == ctx->requests.end() || !it->second->done.load()) return PV_ERR_NOTFOUND;
+  *ns = it->second->t_done.load() - it->second->t_submit;
+  // retire: its memory was returned to the arena by pump()
+  Request* r = it->second;
+  if (r->bytes) { ctx->arena.release(r->arena_off, r->bytes); r->bytes = 0; }
+  delete r;
+  ctx->requests.erase(it);
+  return PV_OK;
+}
+
+const char* pv_strerror(int code) {
+  switch (code) {
+    case PV_OK: return "ok";
+    case PV_ERR_ARG: return "invalid argument";
+    case PV_ERR_CUDA: return "CUDA error";
+    case PV_ERR_CAPACITY: return "capacity exceeded";
+    case PV_ERR_NOMEM: return "out of memory / not admissible";
+    case PV_ERR_TIMEOUT: return "timeout";
+    case PV_ERR_BUSY: return "busy";
+    case PV_ERR_NOTFOUND: return "not found";
+    default: return "unknown error";
+  }
+}
+
+const char* pv_last_cuda_error(const pv_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+uint64_t pv_launch_count(const pv_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+}  // extern "C"

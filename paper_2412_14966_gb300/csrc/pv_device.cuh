@@ -1,0 +1,632 @@
+// pv_device.cuh -- device building blocks of the primary-vertex kernels.
+//
+// Steps (a)-(d1) of the method (extrapolation, histogram, peak search,
+// association) follow a pinned IEEE binary32 operation sequence written with
+// round-to-nearest intrinsics (__fadd_rn, __fmul_rn, __fdiv_rn, __fsqrt_rn),
+// which the compiler never contracts into FMAs.  Histogram weights are
+// integers, so histograms, seeds and track assignments are exact and
+// independent of thread order.  The fit (d2) runs in binary32 with a fixed
+// lane-to-track mapping and a fixed shuffle tree, so its result depends only
+// on the event's own data, not on block size or scheduling.
+#pragma once
+
+#include <cstdint>
+
+#include "pv.h"
+
+namespace pvdev {
+
+constexpr int kOne = PV_ONE;
+constexpr int kMaxSeeds = PV_MAX_SEEDS;
+constexpr int kMaxBins = PV_MAX_BINS;
+constexpr int kMaxTiles = kMaxBins / 32;
+constexpr int kTileWords = kMaxTiles / 32;
+constexpr float kSqrt5 = 2.23606797749979f;   // half-width of the profile in sigma units
+constexpr float kSMin = 1e-6f;                // narrower profiles fill a single bin
+constexpr int kGroup = 8;                     // lanes that fit one vertex
+constexpr int kGroupsPerWarp = 32 / kGroup;
+
+// Derived settings, passed by value to every kernel.
+struct Consts {
+  float z_min, dz, z_gas;
+  float sig_max_pp, sig_max_gas;
+  float x_b, y_b, tx_b, ty_b;
+  float chi2_max, inv_chi2_max, dchi2_tol, dz_tol, max_r_beam;
+  uint32_t thr;             // proto-cluster bin threshold (1/ONE units)
+  uint32_t t_pp, t_gas;     // minimal cluster integrals (1/ONE units)
+  int32_t dip_num, dip_den;
+  int32_t min_assoc_pp, min_assoc_gas, min_pv_pp, min_pv_gas;
+  int32_t nbins, ntiles, gas_bin;
+  int32_t max_iter;
+  int32_t accum_mode;
+};
+
+// ---------------------------------------------------------------------------
+// step (a): extrapolation, Eq. zpocadef, Eq. Vxy (diagonal block), sigma_poca
+
+// Bin of v: floor((v - z_min) / dz); -1 below the range, nbins above it.
+__device__ __forceinline__ int bin_of(float v, const Consts& C) {
+  float q = __fdiv_rn(__fsub_rn(v, C.z_min), C.dz);
+  if (!(q >= 0.0f)) return -1;
+  if (q >= __int2float_rn(C.nbins)) return C.nbins;
+  return static_cast<int>(q);
+}
+
+__device__ __forceinline__ float edge_of(int j, const Consts& C) {
+  return __fadd_rn(C.z_min, __fmul_rn(__int2float_rn(j), C.dz));
+}
+
+struct Prep {
+  float zpoca, sigma;
+  int center, j0, j1;
+  bool filled;
+};
+
+__device__ __forceinline__ Prep prepare_track(float x, float y, float z, float tx, float ty,
+                                              float cxx, float cxtx, float ctxtx,
+                                              const Consts& C) {
+  Prep r;
+  float dtx = __fsub_rn(tx, C.tx_b);
+  float dty = __fsub_rn(ty, C.ty_b);
+  float t2 = __fadd_rn(__fmul_rn(dtx, dtx), __fmul_rn(dty, dty));
+  float xb = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, z));   // beam at the track's z
+  float yb = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, z));
+  float num = __fadd_rn(__fmul_rn(dtx, __fsub_rn(xb, x)), __fmul_rn(dty, __fsub_rn(yb, y)));
+  float zp = __fadd_rn(z, __fdiv_rn(num, t2));
+  float d = __fsub_rn(zp, z);
+  float vxx = __fadd_rn(__fadd_rn(cxx, __fmul_rn(__fmul_rn(2.0f, d), cxtx)),
+                        __fmul_rn(__fmul_rn(d, d), ctxtx));
+  float sig = __fsqrt_rn(__fdiv_rn(vxx, t2));
+  r.zpoca = zp;
+  r.sigma = sig;
+  r.filled = false;
+  r.center = -1;
+  r.j0 = 0;
+  r.j1 = -1;
+  if (!(t2 > 0.0f)) return r;
+  if (!isfinite(zp) || !isfinite(sig)) return r;
+  int c = bin_of(zp, C);
+  if (c < 0 || c >= C.nbins) return r;
+  float smax = (zp < C.z_gas) ? C.sig_max_gas : C.sig_max_pp;
+  if (!(sig <= smax)) return r;
+  float s = __fmul_rn(kSqrt5, sig);
+  if (s < kSMin) s = 0.0f;
+  r.filled = true;
+  r.center = c;
+  r.j0 = bin_of(__fsub_rn(zp, s), C);
+  r.j1 = bin_of(__fadd_rn(zp, s), C);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// step (b): integer profile = quantised cubic CDF of the variance-matched
+// Epanechnikov kernel, F(u) = 1/2 + u (3/4 - u^2/4), u in [-1, 1].
+
+__device__ __forceinline__ int quant_cdf(float u) {
+  if (!(u > -1.0f)) return 0;
+  if (u >= 1.0f) return kOne;
+  float a = __fmul_rn(u, u);
+  float b = __fmul_rn(0.25f, a);
+  float c = __fsub_rn(0.75f, b);
+  float d = __fmul_rn(u, c);
+  float F = __fadd_rn(0.5f, d);
+  int q = __float2int_rn(__fmul_rn(F, static_cast<float>(kOne)));
+  q = q < 0 ? 0 : q;
+  return q > kOne ? kOne : q;
+}
+
+// Add one filled track's profile to hist (shared or global memory).
+__device__ __forceinline__ void fill_profile(uint32_t* hist, float zpoca, float sigma, int j0, int j1,
+                                             const Consts& C) {
+  float s = __fmul_rn(kSqrt5, sigma);
+  if (s < kSMin) s = 0.0f;
+  float inv_s = (s > 0.0f) ? __fdiv_rn(1.0f, s) : 0.0f;
+  int qprev = 0;
+  for (int j = j0; j <= j1; ++j) {
+    int qnext;
+    if (j == j1) {
+      qnext = kOne;
+    } else {
+      float e = edge_of(j + 1, C);
+      qnext = quant_cdf(__fmul_rn(__fsub_rn(e, zpoca), inv_s));
+    }
+    qnext = qnext < qprev ? qprev : qnext;
+    int w = qnext - qprev;
+    if (w > 0 && j >= 0 && j < C.nbins) atomicAdd(hist + j, static_cast<uint32_t>(w));
+    qprev = qnext;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// step (c): proto-clusters, dip splitting in z order, seeds
+
+struct SeedOut {   // shared-memory seed table of one event
+  int lo[kMaxSeeds], hi[kMaxSeeds], bin[kMaxSeeds];
+  float z[kMaxSeeds], x[kMaxSeeds], y[kMaxSeeds];
+};
+
+// Walk proto-cluster [a, b] of N; calls emit(lo, hi, integral) per piece in
+// z order.  Splits at the leftmost bin of a significant minimum between the
+// running maximum of the open piece (L) and the next maximum (R) if both the
+// piece [s, m] and the rest [m+1, b] hold the minimal integral.
+template <class Emit>
+__device__ void split_walk(const uint32_t* N, int a, int b, const Consts& C, Emit&& emit) {
+  uint64_t total = 0;
+  for (int i = a; i <= b; ++i) total += N[i];
+  int s = a;
+  uint64_t pre_s = 0;                 // sum over [a, s)
+  int top = a;
+  uint64_t pre = N[a];                // sum over [a, top]
+  while (top < b && N[top + 1] >= N[top]) { ++top; pre += N[top]; }
+  uint32_t L = N[top];
+  while (top < b) {
+    int j = top, m = top;
+    uint64_t pre_j = pre, pre_m = pre;
+    while (j < b && N[j + 1] <= N[j]) {
+      ++j;
+      pre_j += N[j];
+      if (N[j] < N[j - 1]) { m = j; pre_m = pre_j; }
+    }
+    if (j == b) break;
+    int k = j;
+    uint64_t pre_k = pre_j;
+    while (k < b && N[k + 1] >= N[k]) { ++k; pre_k += N[k]; }
+    uint32_t R = N[k];
+    uint32_t lower = L < R ? L : R;
+    bool split = false;
+    if (static_cast<uint64_t>(C.dip_den) * N[m] < static_cast<uint64_t>(C.dip_num) * lower) {
+      uint64_t T = (m < C.gas_bin) ? C.t_gas : C.t_pp;
+      if (pre_m - pre_s >= T && total - pre_m >= T) split = true;
+    }
+    if (split) {
+      emit(s, m, pre_m - pre_s);
+      s = m + 1;
+      pre_s = pre_m;
+      L = R;
+    } else if (R > L) {
+      L = R;
+    }
+    top = k;
+    pre = pre_k;
+  }
+  emit(s, b, total - pre_s);
+}
+
+__device__ __forceinline__ int argmax_bins(const uint32_t* N, int lo, int hi) {
+  int best = lo;
+  uint32_t bv = N[lo];
+  for (int i = lo + 1; i <= hi; ++i)
+    if (N[i] > bv) { bv = N[i]; best = i; }
+  return best;
+}
+
+__device__ __forceinline__ bool keep_piece(const uint32_t* N, int lo, int hi, uint64_t integral,
+                                           const Consts& C, int* im) {
+  *im = argmax_bins(N, lo, hi);
+  uint64_t T = (*im < C.gas_bin) ? C.t_gas : C.t_pp;
+  return integral >= T;
+}
+
+// z_seed = z_mid(i) + delta dz, delta from the exact bin contents in binary64
+// (Sec. 3.3), rounded once to binary32.
+__device__ __forceinline__ float seed_z(const uint32_t* N, int i, const Consts& C) {
+  long long nm = (i > 0) ? static_cast<long long>(N[i - 1]) : 0;
+  long long np = (i + 1 < C.nbins) ? static_cast<long long>(N[i + 1]) : 0;
+  long long ni = static_cast<long long>(N[i]);
+  long long num = np - nm;
+  long long den = 2 * ni - np - nm;
+  double delta = 0.0;
+  if (den > 0) delta = __dmul_rn(0.5, __ddiv_rn(static_cast<double>(num), static_cast<double>(den)));
+  double t1 = static_cast<double>(i) + 0.5;
+  double t2 = __dmul_rn(t1, static_cast<double>(C.dz));
+  double zmid = __dadd_rn(static_cast<double>(C.z_min), t2);
+  double t3 = __dmul_rn(delta, static_cast<double>(C.dz));
+  return __double2float_rn(__dadd_rn(zmid, t3));
+}
+
+// Warp-cooperative peak search over a histogram N (shared or global).  If
+// tmask is non-null only tiles (32 bins) whose bit is set can hold non-zero
+// bins; otherwise every tile is scanned.  pc_lo / pc_hi are a 128-entry ring
+// in shared memory.  Writes up to cap seeds into S in z order and returns the
+// number found (which may exceed cap).  All 32 lanes must call it.
+__device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
+                               SeedOut* S, int cap, int* pc_lo, int* pc_hi) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int n_seeds = 0;
+  int n_starts = 0, n_ends = 0, n_done = 0;
+
+  auto process = [&](int count) {
+    // lane j walks proto-cluster n_done + j (pass 1 counts kept pieces)
+    int a = 0, b = -1;
+    if (lane < count) {
+      a = pc_lo[(n_done + lane) & 127];
+      b = pc_hi[(n_done + lane) & 127];
+    }
+    int kept = 0;
+    if (lane < count) {
+      split_walk(N, a, b, C, [&](int lo, int hi, uint64_t integral) {
+        int im;
+        if (keep_piece(N, lo, hi, integral, C, &im)) ++kept;
+      });
+    }
+    int incl = kept;
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = n_seeds + incl - kept;
+    if (lane < count && kept > 0 && pos < cap) {
+      split_walk(N, a, b, C, [&](int lo, int hi, uint64_t integral) {
+        int im;
+        if (keep_piece(N, lo, hi, integral, C, &im)) {
+          if (pos < cap) {
+            float zs = seed_z(N, im, C);
+            S->lo[pos] = lo;
+            S->hi[pos] = hi;
+            S->bin[pos] = im;
+            S->z[pos] = zs;
+            S->x[pos] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
+            S->y[pos] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
+          }
+          ++pos;
+        }
+      });
+    }
+    n_seeds += total;
+    n_done += count;
+    __syncwarp();
+  };
+
+  for (int w = 0; w < (C.ntiles + 31) / 32; ++w) {
+    uint32_t m;
+    if (tmask) {
+      m = tmask[w];
+    } else {
+      int left = C.ntiles - 32 * w;
+      m = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+    }
+    while (m) {
+      int tb = __ffs(m) - 1;
+      m &= m - 1;
+      int bin = (w * 32 + tb) * 32 + lane;
+      uint32_t v = (bin < C.nbins) ? N[bin] : 0u;
+      uint32_t vp = (bin >= 1 && bin - 1 < C.nbins) ? N[bin - 1] : 0u;
+      uint32_t vn = (bin + 1 < C.nbins) ? N[bin + 1] : 0u;
+      bool above = v > C.thr;
+      unsigned starts = __ballot_sync(0xffffffffu, above && !(vp > C.thr));
+      unsigned ends = __ballot_sync(0xffffffffu, above && !(vn > C.thr));
+      if (starts & (1u << lane)) pc_lo[(n_starts + __popc(starts & lt)) & 127] = bin;
+      if (ends & (1u << lane)) pc_hi[(n_ends + __popc(ends & lt)) & 127] = bin;
+      n_starts += __popc(starts);
+      n_ends += __popc(ends);
+      __syncwarp();
+      while (n_ends - n_done >= 32) process(32);
+    }
+  }
+  if (n_ends - n_done > 0) process(n_ends - n_done);
+  return n_seeds;
+}
+
+// ---------------------------------------------------------------------------
+// step (d1): association with the removal loop, block-cooperative.
+//
+// center[t]: center bin or -1; cid[t] receives the index among the surviving
+// seeds (z order) or -1.  S holds K seeds on entry and the survivors,
+// compacted in z order, on exit.  cnt receives the tracks per survivor.
+// Scratch arrays alive/part live in shared memory.  Returns the survivors.
+template <typename CenterT, typename CidT>
+__device__ int block_associate(const CenterT* center, CidT* cid, int n, SeedOut* S, int K,
+                               const Consts& C, int* alive, int* part, int* cnt, int* flag) {
+  const int tid = threadIdx.x;
+  const int nt = blockDim.x;
+  if (tid < K) alive[tid] = tid;
+  __shared__ int s_ka;
+  if (tid == 0) s_ka = K;
+  __syncthreads();
+  for (;;) {
+    int ka = s_ka;
+    if (tid + 1 < ka) part[tid] = (S->hi[alive[tid]] + S->lo[alive[tid + 1]]) >> 1;
+    if (tid < ka) cnt[tid] = 0;
+    __syncthreads();
+    for (int t = tid; t < n; t += nt) {
+      int c = static_cast<int>(center[t]);
+      int q = -1;
+      if (c >= 0 && ka > 0) {
+        int lo = 0, hi = ka - 1;        // number of partition points < c
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (part[mid] < c) lo = mid + 1; else hi = mid;
+        }
+        q = lo;
+        atomicAdd(cnt + q, 1);
+      }
+      cid[t] = static_cast<CidT>(q);
+    }
+    __syncthreads();
+    if (tid < 32) {
+      // fewest tracks among clusters below their threshold, lowest z on ties
+      long long best = 0x7fffffffffffffffLL;
+      for (int q = tid; q < ka; q += 32) {
+        int gas = S->bin[alive[q]] < C.gas_bin;
+        int need = gas ? C.min_assoc_gas : C.min_assoc_pp;
+        if (cnt[q] < need) {
+          long long key = (static_cast<long long>(cnt[q]) << 8) | q;
+          best = key < best ? key : best;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v < best ? v : best;
+      }
+      if (tid == 0) {
+        if (best == 0x7fffffffffffffffLL) {
+          *flag = 0;
+        } else {
+          int q = static_cast<int>(best & 0xff);
+          for (int r = q; r + 1 < ka; ++r) alive[r] = alive[r + 1];
+          s_ka = ka - 1;
+          *flag = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (!*flag) break;
+  }
+  int ka = s_ka;
+  // compact survivors in z order (alive is increasing)
+  if (tid < 32) {
+    int lo[2], hi[2], bn[2];
+    float z[2], x[2], y[2];
+    for (int h = 0; h < 2; ++h) {
+      int q = tid + 32 * h;
+      if (q < ka) {
+        int k = alive[q];
+        lo[h] = S->lo[k]; hi[h] = S->hi[k]; bn[h] = S->bin[k];
+        z[h] = S->z[k]; x[h] = S->x[k]; y[h] = S->y[k];
+      }
+    }
+    __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+      int q = tid + 32 * h;
+      if (q < ka) {
+        S->lo[q] = lo[h]; S->hi[q] = hi[h]; S->bin[q] = bn[h];
+        S->z[q] = z[h]; S->x[q] = x[h]; S->y[q] = y[h];
+      }
+    }
+  }
+  __syncthreads();
+  return ka;
+}
+
+// ---------------------------------------------------------------------------
+// step (d2): per-track fit inputs relative to the seed, and the group fit
+
+struct FitTrack {            // 24 bytes: position at z_seed relative to the seed, slopes, weights
+  float X, Y, tx, ty;
+  float wx, wy;              // 1/V_xx, 1/V_yy at z_seed; 0 marks an unusable track
+};
+
+__device__ __forceinline__ void make_fit_track(float x, float y, float z, float tx, float ty,
+                                               float cxx, float cxtx, float ctxtx,
+                                               float cyy, float cyty, float ctyty,
+                                               float xs, float ys, float zs,
+                                               float4* A, float2* W) {
+  float d = zs - z;
+  float vxx = cxx + 2.0f * d * cxtx + d * d * ctxtx;
+  float vyy = cyy + 2.0f * d * cyty + d * d * ctyty;
+  float X = x + d * tx - xs;
+  float Y = y + d * ty - ys;
+  bool ok = (vxx > 0.0f) && (vyy > 0.0f) && isfinite(vxx) && isfinite(vyy) && isfinite(X) &&
+            isfinite(Y) && isfinite(tx) && isfinite(ty);
+  if (ok) {
+    *A = make_float4(X, Y, tx, ty);
+    *W = make_float2(1.0f / vxx, 1.0f / vyy);
+  } else {
+    *A = make_float4(0.f, 0.f, 0.f, 0.f);
+    *W = make_float2(0.f, 0.f);
+  }
+}
+
+struct VertexOut {
+  float x, y, z;
+  float cov[6];
+  float chi2, ndof;
+  int n_tracks, n_iter, status;
+};
+
+// Sum over the 8 lanes of a group (xor tree; identical on all 8 lanes).
+__device__ __forceinline__ float group_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+__device__ __forceinline__ int group_sum_i(int v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// Error-free transformation: s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// Compensated accumulation (Kahan-Babuska-Neumaier style with TwoSum).
+struct CSum {
+  float hi, lo;
+  __device__ __forceinline__ void add(float v) {
+    float s, e;
+    two_sum(hi, v, s, e);
+    hi = s;
+    lo += e;
+  }
+  __device__ __forceinline__ float value() const { return hi + lo; }
+};
+__device__ __forceinline__ float group_sum_c(CSum v) {
+  // reduce (hi, lo) pairs with TwoSum at every level
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    float oh = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    float ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    float s, e;
+    two_sum(v.hi, oh, s, e);
+    v.hi = s;
+    v.lo = v.lo + ol + e;
+  }
+  return v.hi + v.lo;
+}
+
+// Fit of one vertex per 8-lane group.  Every lane of the warp must call it
+// (shuffles); lanes of groups without a vertex pass cntk = -1.  Track s of the
+// vertex (s = 0 .. cntk-1, in track-index order) is handled by lane s mod 8 of
+// the group.  The result lands in *out on every lane of the group.
+template <bool kKahan>
+__device__ void group_fit(const float4* A, const float2* W, int cntk, const Consts& C,
+                          VertexOut* out) {
+  const int r = threadIdx.x & (kGroup - 1);
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  bool done = cntk < 0;
+  int status = 0, n_iter = 0;
+  float Sxx = 0, Syy = 0, Sxz = 0, Syz = 0, c2sum = 0, sw = 0, dchi2 = 0;
+  float ix = 0, iy = 0, ux = 0, uy = 0, is = 0;
+  int nw = 0;
+  for (int it = 1; it <= C.max_iter; ++it) {
+    float v[10];
+    int cnt_w = 0;
+    if (kKahan) {
+      CSum acc[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) acc[q] = CSum{0.f, 0.f};
+      if (!done) {
+        for (int s = r; s < cntk; s += kGroup) {
+          float4 a = A[s];
+          float2 w2 = W[s];
+          if (!(w2.x > 0.0f)) continue;
+          float rx = a.x + az * a.z - ax;
+          float ry = a.y + az * a.w - ay;
+          float c2 = rx * rx * w2.x + ry * ry * w2.y;
+          float w = 0.f;
+          if (c2 < C.chi2_max) { float f = 1.0f - c2 * C.inv_chi2_max; w = f * f; }
+          if (w > 0.f) {
+            float wx = w * w2.x, wy = w * w2.y;
+            acc[0].add(wx); acc[1].add(wy);
+            acc[2].add(wx * a.z); acc[3].add(wy * a.w);
+            acc[4].add(wx * a.z * a.z + wy * a.w * a.w);
+            acc[5].add(wx * rx); acc[6].add(wy * ry);
+            acc[7].add(wx * a.z * rx + wy * a.w * ry);
+            acc[8].add(w * c2); acc[9].add(w);
+            ++cnt_w;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 10; ++q) v[q] = group_sum_c(acc[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) v[q] = 0.f;
+      if (!done) {
+        for (int s = r; s < cntk; s += kGroup) {
+          float4 a = A[s];
+          float2 w2 = W[s];
+          if (!(w2.x > 0.0f)) continue;
+          float rx = a.x + az * a.z - ax;
+          float ry = a.y + az * a.w - ay;
+          float c2 = rx * rx * w2.x + ry * ry * w2.y;
+          float w = 0.f;
+          if (c2 < C.chi2_max) { float f = 1.0f - c2 * C.inv_chi2_max; w = f * f; }
+          if (w > 0.f) {
+            float wx = w * w2.x, wy = w * w2.y;
+            v[0] += wx; v[1] += wy;
+            v[2] += wx * a.z; v[3] += wy * a.w;
+            v[4] += wx * a.z * a.z + wy * a.w * a.w;
+            v[5] += wx * rx; v[6] += wy * ry;
+            v[7] += wx * a.z * rx + wy * a.w * ry;
+            v[8] += w * c2; v[9] += w;
+            ++cnt_w;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 10; ++q) v[q] = group_sum(v[q]);
+    }
+    cnt_w = group_sum_i(cnt_w);
+    if (!done) {
+      // M = [[Sxx,0,-Sxz],[0,Syy,-Syz],[-Sxz,-Syz,Szz]], g = (-bx, -by, bz)
+      float sxx = v[0], syy = v[1], sxz = v[2], syz = v[3], szz = v[4];
+      float bx = v[5], by = v[6], bz = v[7];
+      n_iter = it;
+      Sxx = sxx; Syy = syy; Sxz = sxz; Syz = syz;
+      c2sum = v[8]; sw = v[9]; nw = cnt_w;
+      float s_ = 0.f;
+      bool ok = sxx > 0.f && syy > 0.f && isfinite(sxx) && isfinite(syy);
+      if (ok) {
+        ix = 1.0f / sxx;
+        iy = 1.0f / syy;
+        ux = sxz * ix;
+        uy = syz * iy;
+        s_ = szz - sxz * ux - syz * uy;      // Schur complement: the z pivot
+        ok = s_ > 0.f && isfinite(s_);
+      }
+      if (!ok) {
+        status = PV_ST_SINGULAR;
+        dchi2 = 0.f;
+        done = true;
+      } else {
+        is = 1.0f / s_;
+        float dz = (ux * bx + uy * by - bz) * is;
+        float dx = (bx + sxz * dz) * ix;
+        float dy = (by + syz * dz) * iy;
+        dchi2 = -bx * dx - by * dy + bz * dz;
+        ax += dx;
+        ay += dy;
+        az += dz;
+        if (fabsf(dchi2) < C.dchi2_tol && fabsf(dz) < C.dz_tol) {
+          status = PV_ST_CONVERGED;
+          done = true;
+        } else if (it == C.max_iter) {
+          status = PV_ST_MAXITER;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+  if (cntk < 0) return;
+  out->x = ax;       // relative to the seed; the caller adds the seed position
+  out->y = ay;
+  out->z = az;
+  out->cov[0] = ix + ux * ux * is;   // xx
+  out->cov[1] = ux * uy * is;        // xy
+  out->cov[2] = iy + uy * uy * is;   // yy
+  out->cov[3] = ux * is;             // xz
+  out->cov[4] = uy * is;             // yz
+  out->cov[5] = is;                  // zz
+  out->chi2 = c2sum + dchi2;
+  out->ndof = 2.0f * sw - 3.0f;
+  out->n_tracks = nw;
+  out->n_iter = n_iter;
+  out->status = status == 0 ? PV_ST_MAXITER : status;
+}
+
+// Final selection (Sec. 3.5): pp vertices farther than max_r_beam from the
+// beamline and vertices with too few tracks are flagged; the rest accepted.
+__device__ __forceinline__ int select_vertex(float x, float y, float z, int n_tracks, int status,
+                                             const Consts& C) {
+  if (status & PV_ST_SINGULAR) return status;
+  bool gas = z < C.z_gas;
+  if (!gas) {
+    float bx = C.x_b + C.tx_b * z, by = C.y_b + C.ty_b * z;
+    float r = sqrtf((x - bx) * (x - bx) + (y - by) * (y - by));
+    if (r > C.max_r_beam) status |= PV_ST_REJ_BEAM;
+  }
+  int need = gas ? C.min_pv_gas : C.min_pv_pp;
+  if (n_tracks < need) status |= PV_ST_REJ_NTRK;
+  if (!(status & (PV_ST_REJ_BEAM | PV_ST_REJ_NTRK))) status |= PV_ST_ACCEPTED;
+  return status;
+}
+
+}  // namespace pvdev

@@ -1,0 +1,532 @@
+// pv_kernels.cu -- sm_103a kernels of the primary-vertex library.
+//
+// Fused path: one persistent kernel, one event at a time per CTA, events taken
+// from a global work counter (uneven event sizes balance themselves).  Per
+// event the CTA keeps the z histogram in shared memory (cleared only where
+// tracks wrote, tracked by a 32-bin tile mask), finds seeds with warp ballots,
+// associates tracks, and fits all vertices with 8-lane groups.  Per-track
+// state stays in shared memory for events up to kSmallCap tracks and in an
+// L2-resident global scratch for larger events, so no event size is refused.
+//
+// Plain path: one kernel per step (extrapolate / histogram / peaks /
+// associate / fit), one CTA per event, histograms and per-track state in
+// global memory: the per-step design the fused path is measured against.
+#include "pv_kernels.cuh"
+
+namespace pvk {
+
+using namespace pvdev;
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of the fused kernel
+
+struct Layout {
+  size_t A, W, hist, tmask, seeds, pc_lo, pc_hi, alive, part, cnt, voff, base, center, cid, slot,
+      misc, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ inline Layout make_layout(int nbins, int mode) {
+  Layout L;
+  size_t o = 0;
+  const bool fit = (mode & kFit) != 0;
+  const bool find = (mode & kFind) != 0;
+  const int ntiles = (nbins + 31) / 32;
+  L.A = o;      o += fit ? sizeof(float4) * kSmallCap : 0;
+  L.W = o;      o += fit ? sizeof(float2) * kSmallCap : 0;
+  L.hist = o;   o += find ? sizeof(uint32_t) * ntiles * 32 : 0;
+  L.tmask = o;  o += sizeof(uint32_t) * kTileWords;
+  L.seeds = o;  o += align_up(sizeof(SeedOut), 16);
+  L.pc_lo = o;  o += sizeof(int) * 128;
+  L.pc_hi = o;  o += sizeof(int) * 128;
+  L.alive = o;  o += sizeof(int) * kMaxSeeds;
+  L.part = o;   o += sizeof(int) * kMaxSeeds;
+  L.cnt = o;    o += sizeof(int) * kMaxSeeds;
+  L.voff = o;   o += sizeof(int) * kMaxSeeds;
+  L.base = o;   o += sizeof(int) * kMaxSeeds;
+  L.center = o; o += sizeof(int) * kSmallCap;
+  L.cid = o;    o += sizeof(int) * kSmallCap;
+  L.slot = o;   o += sizeof(int) * kSmallCap;
+  L.misc = o;   o += sizeof(int) * 8;
+  L.total = align_up(o, 16);
+  return L;
+}
+
+size_t fused_smem_bytes(int nbins, int mode) { return make_layout(nbins, mode).total; }
+
+// ---------------------------------------------------------------------------
+// pieces shared by the fused and the plain kernels
+
+// Exclusive scan of cnt[0..K) into voff and base (warp 0 only, K <= 64).
+__device__ __forceinline__ void warp_offsets(const int* cnt, int K, int* voff, int* base) {
+  const int lane = threadIdx.x & 31;
+  int c0 = lane < K ? cnt[lane] : 0;
+  int c1 = lane + 32 < K ? cnt[lane + 32] : 0;
+  int s0 = c0;
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, s0, o);
+    if (lane >= o) s0 += v;
+  }
+  int tot0 = __shfl_sync(0xffffffffu, s0, 31);
+  int s1 = c1;
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, s1, o);
+    if (lane >= o) s1 += v;
+  }
+  if (lane < K) { voff[lane] = s0 - c0; base[lane] = s0 - c0; }
+  if (lane + 32 < K) { voff[lane + 32] = tot0 + s1 - c1; base[lane + 32] = tot0 + s1 - c1; }
+}
+
+// Stable placement of tracks by vertex (track-index order inside a vertex);
+// warp 0 only.  base[] is advanced.
+__device__ __forceinline__ void warp_slots(const int* cid, int n, int* base, int* slot) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int t0 = 0; t0 < n; t0 += 32) {
+    int t = t0 + lane;
+    int c = t < n ? cid[t] : -1;
+    unsigned peers = __match_any_sync(0xffffffffu, c);
+    int rank = __popc(peers & lt);
+    int leader = __ffs(peers) - 1;
+    int b = c >= 0 ? base[c] : 0;
+    __syncwarp();
+    if (c >= 0) {
+      slot[t] = b + rank;
+      if (lane == leader) base[c] = b + __popc(peers);
+    }
+    __syncwarp();
+  }
+}
+
+// Fit every vertex of one event (block-cooperative).  A, W: per-track fit
+// inputs in vertex order; voff/cnt: vertex ranges.
+__device__ void block_fit_event(const Consts& C, const SeedOut* S, int Ka, const int* voff,
+                                const int* cnt, const float4* A, const float2* W,
+                                const OutPtrs& O, int e) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  for (int vb = warp * kGroupsPerWarp; vb < Ka; vb += nw * kGroupsPerWarp) {
+    int k = vb + (lane >> 3);
+    bool has = k < Ka;
+    int cntk = has ? cnt[k] : -1;
+    int o = has ? voff[k] : 0;
+    VertexOut v;
+    if (C.accum_mode == PV_ACCUM_KAHAN)
+      group_fit<true>(A + o, W + o, cntk, C, &v);
+    else
+      group_fit<false>(A + o, W + o, cntk, C, &v);
+    if (has && (lane & 7) == 0) {
+      size_t q = static_cast<size_t>(e) * O.cap + k;
+      float x = S->x[k] + v.x, y = S->y[k] + v.y, z = S->z[k] + v.z;
+      int st = select_vertex(x, y, z, v.n_tracks, v.status, C);
+      O.x[q] = x;
+      O.y[q] = y;
+      O.z[q] = z;
+      if (O.cov) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) O.cov[q * 6 + c] = v.cov[c];
+      }
+      if (O.chi2) O.chi2[q] = v.chi2;
+      if (O.ndof) O.ndof[q] = v.ndof;
+      if (O.n_tracks) O.n_tracks[q] = v.n_tracks;
+      if (O.n_iter) O.n_iter[q] = v.n_iter;
+      if (O.status) O.status[q] = st;
+    }
+  }
+}
+
+// Per-track fit inputs in vertex order.
+__device__ __forceinline__ void block_fit_inputs(const TrackPtrs& T, int64_t b0, int n,
+                                                 const int* cid, const int* slot, const SeedOut* S,
+                                                 float4* A, float2* W) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    int c = cid[t];
+    if (c < 0) continue;
+    int64_t i = b0 + t;
+    int s = slot[t];
+    make_fit_track(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i], T.cxtx[i], T.ctxtx[i],
+                   T.cyy[i], T.cyty[i], T.ctyty[i], S->x[c], S->y[c], S->z[c], A + s, W + s);
+  }
+}
+
+__device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tracks) {
+  return b0 < 0 || b1 < b0 || b1 > n_tracks || b1 - b0 > 0x7fffffffLL;
+}
+
+// ---------------------------------------------------------------------------
+// fused persistent kernel
+
+template <int MODE>
+__global__ void __launch_bounds__(kFusedThreads)
+fused_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G, int* work_counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Layout Lo = make_layout(C.nbins, MODE);
+  float4* sA = reinterpret_cast<float4*>(smem + Lo.A);
+  float2* sW = reinterpret_cast<float2*>(smem + Lo.W);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + Lo.hist);
+  uint32_t* tmask = reinterpret_cast<uint32_t*>(smem + Lo.tmask);
+  SeedOut* S = reinterpret_cast<SeedOut*>(smem + Lo.seeds);
+  int* pc_lo = reinterpret_cast<int*>(smem + Lo.pc_lo);
+  int* pc_hi = reinterpret_cast<int*>(smem + Lo.pc_hi);
+  int* alive = reinterpret_cast<int*>(smem + Lo.alive);
+  int* part = reinterpret_cast<int*>(smem + Lo.part);
+  int* cnt = reinterpret_cast<int*>(smem + Lo.cnt);
+  int* voff = reinterpret_cast<int*>(smem + Lo.voff);
+  int* base = reinterpret_cast<int*>(smem + Lo.base);
+  int* s_center = reinterpret_cast<int*>(smem + Lo.center);
+  int* s_cid = reinterpret_cast<int*>(smem + Lo.cid);
+  int* s_slot = reinterpret_cast<int*>(smem + Lo.slot);
+  int* misc = reinterpret_cast<int*>(smem + Lo.misc);
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  constexpr int NT = kFusedThreads;
+  constexpr int NW = NT / 32;
+
+  if (MODE & kFind) {
+    for (int i = tid; i < C.ntiles * 32; i += NT) hist[i] = 0u;
+  }
+  if (tid < kTileWords) tmask[tid] = 0u;
+  __syncthreads();
+
+  for (int iter = 0;; ++iter) {
+    if (tid == 0) misc[iter & 1] = atomicAdd(work_counter, 1);
+    __syncthreads();
+    const int e = misc[iter & 1];
+    if (e >= T.n_events) break;
+    const int64_t b0 = T.off[e], b1 = T.off[e + 1];
+    if (offsets_bad(b0, b1, T.n_tracks)) {
+      if (tid == 0) {
+        O.n_per_event[e] = 0;
+        if (O.event_status) O.event_status[e] = PV_EV_BAD_OFFSETS;
+      }
+      continue;   // uniform: every thread read the same offsets
+    }
+    const int n = static_cast<int>(b1 - b0);
+    const bool small = n <= kSmallCap;
+    int* center = small ? s_center : G.center + b0;
+    int* cid = small ? s_cid : G.cid + b0;
+    int* slot = small ? s_slot : G.slot + b0;
+    float4* A = small ? sA : G.A + b0;
+    float2* W = small ? sW : G.W + b0;
+    int Ka = 0;
+
+    if (MODE & kFind) {
+      // (a) + (b): extrapolate, mark tiles, fill the shared histogram
+      for (int t = tid; t < n; t += NT) {
+        const int64_t i = b0 + t;
+        Prep p = prepare_track(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i], T.cxtx[i],
+                               T.ctxtx[i], C);
+        center[t] = p.filled ? p.center : -1;
+        if (p.filled) {
+          int q0 = (p.j0 < 0 ? 0 : p.j0) >> 5;
+          int q1 = (p.j1 >= C.nbins ? C.nbins - 1 : p.j1) >> 5;
+          for (int q = q0; q <= q1; ++q) {
+            uint32_t bit = 1u << (q & 31);
+            if (!(tmask[q >> 5] & bit)) atomicOr(tmask + (q >> 5), bit);
+          }
+          fill_profile(hist, p.zpoca, p.sigma, p.j0, p.j1, C);
+        }
+      }
+      __syncthreads();
+      // (c): seeds from the touched tiles (warp 0)
+      if (warp == 0) {
+        int K = warp_find_seeds(hist, tmask, C, S, O.cap, pc_lo, pc_hi);
+        if (lane == 0) misc[2] = K;
+      }
+      __syncthreads();
+      const int Kall = misc[2];
+      const int K = Kall < O.cap ? Kall : O.cap;
+      // clear the touched tiles for the next event
+      for (int q = warp; q < C.ntiles; q += NW)
+        if ((tmask[q >> 5] >> (q & 31)) & 1u) hist[q * 32 + lane] = 0u;
+      // (d1): association with the removal loop
+      Ka = block_associate(center, cid, n, S, K, C, alive, part, cnt, misc + 3);
+      if (tid < kTileWords) tmask[tid] = 0u;
+      for (int t = tid; t < n; t += NT) O.track_vertex[b0 + t] = cid[t];
+      if (tid == 0) {
+        O.n_per_event[e] = Ka;
+        if (O.event_status) O.event_status[e] = Kall > O.cap ? PV_EV_SEED_OVERFLOW : 0;
+      }
+      if (tid < Ka) {
+        size_t q = static_cast<size_t>(e) * O.cap + tid;
+        if (O.bin_lo) O.bin_lo[q] = S->lo[tid];
+        if (O.bin_hi) O.bin_hi[q] = S->hi[tid];
+        if (O.bin_max) O.bin_max[q] = S->bin[tid];
+        if (MODE == kFind) {
+          O.x[q] = S->x[tid];
+          O.y[q] = S->y[tid];
+          O.z[q] = S->z[tid];
+        }
+      }
+    } else {
+      // fit only: seeds and assignment from the caller
+      int K = SP.n_per_event[e];
+      const int capk = SP.cap < kMaxSeeds ? SP.cap : kMaxSeeds;
+      K = K < 0 ? 0 : (K > capk ? capk : K);
+      if (tid < K) {
+        size_t q = static_cast<size_t>(e) * SP.cap + tid;
+        S->x[tid] = SP.x[q];
+        S->y[tid] = SP.y[q];
+        S->z[tid] = SP.z[q];
+        cnt[tid] = 0;
+      }
+      __syncthreads();
+      for (int t = tid; t < n; t += NT) {
+        int c = SP.track_vertex[b0 + t];
+        c = (c >= 0 && c < K) ? c : -1;
+        cid[t] = c;
+        if (c >= 0) atomicAdd(cnt + c, 1);
+        if (O.track_vertex != SP.track_vertex) O.track_vertex[b0 + t] = c;
+      }
+      if (tid == 0 && O.n_per_event != SP.n_per_event) O.n_per_event[e] = K;
+      Ka = K;
+      __syncthreads();
+    }
+
+    if (MODE & kFit) {
+      if (warp == 0) warp_offsets(cnt, Ka, voff, base);
+      __syncthreads();
+      if (warp == 0) warp_slots(cid, n, base, slot);
+      __syncthreads();
+      block_fit_inputs(T, b0, n, cid, slot, S, A, W);
+      __syncthreads();
+      block_fit_event(C, S, Ka, voff, cnt, A, W, O, e);
+    }
+  }
+}
+
+int fused_blocks_per_sm(int nbins, int mode) {
+  int blocks = 0;
+  size_t sm = fused_smem_bytes(nbins, mode);
+  cudaError_t err;
+  if (mode == kFind)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<kFind>, kFusedThreads, sm);
+  else if (mode == kFit)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<kFit>, kFusedThreads, sm);
+  else
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<kFindFit>, kFusedThreads, sm);
+  if (err != cudaSuccess) return 0;
+  return blocks;
+}
+
+cudaError_t fused_setup(int nbins) {
+  cudaError_t err;
+  err = cudaFuncSetAttribute(fused_kernel<kFind>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fused_smem_bytes(nbins, kFind));
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(fused_kernel<kFit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fused_smem_bytes(nbins, kFit));
+  if (err != cudaSuccess) return err;
+  return cudaFuncSetAttribute(fused_kernel<kFindFit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fused_smem_bytes(nbins, kFindFit));
+}
+
+cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
+                         const OutPtrs& O, const TrackScratch& ws, int* work_counter, int grid,
+                         cudaStream_t st) {
+  size_t sm = fused_smem_bytes(C.nbins, mode);
+  cudaError_t err = cudaMemsetAsync(work_counter, 0, sizeof(int), st);
+  if (err != cudaSuccess) return err;
+  if (mode == kFind)
+    fused_kernel<kFind><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+  else if (mode == kFit)
+    fused_kernel<kFit><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+  else
+    fused_kernel<kFindFit><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// plain per-step kernels
+
+__global__ void plain_extrapolate_kernel(Consts C, TrackPtrs T, float* zpoca, float* sigma,
+                                         int32_t* center, int32_t* j0, int32_t* j1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T.n_tracks;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    Prep p = prepare_track(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i], T.cxtx[i],
+                           T.ctxtx[i], C);
+    if (zpoca) zpoca[i] = p.zpoca;
+    if (sigma) sigma[i] = p.sigma;
+    if (center) center[i] = p.filled ? p.center : -1;
+    if (j0) j0[i] = p.j0;
+    if (j1) j1[i] = p.j1;
+  }
+}
+
+__global__ void plain_hist_kernel(Consts C, TrackPtrs T, const float* zpoca, const float* sigma,
+                                  const int32_t* center, const int32_t* j0, const int32_t* j1,
+                                  uint32_t* hist) {
+  const int e = blockIdx.x;
+  const int64_t b0 = T.off[e], b1 = T.off[e + 1];
+  if (offsets_bad(b0, b1, T.n_tracks)) return;
+  uint32_t* h = hist + static_cast<size_t>(e) * C.nbins;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x)
+    if (center[i] >= 0) fill_profile(h, zpoca[i], sigma[i], j0[i], j1[i], C);
+}
+
+__global__ void __launch_bounds__(32)
+plain_peaks_kernel(Consts C, TrackPtrs T, const uint32_t* hist, int cap, int32_t* seed_n,
+                   int32_t* seed_lo, int32_t* seed_hi, int32_t* seed_bin, float* seed_z,
+                   int32_t* ev_status) {
+  __shared__ SeedOut S;
+  __shared__ int pc_lo[128], pc_hi[128];
+  const int e = blockIdx.x;
+  const int64_t b0 = T.off[e], b1 = T.off[e + 1];
+  const int lane = threadIdx.x;
+  if (offsets_bad(b0, b1, T.n_tracks)) {
+    if (lane == 0) { seed_n[e] = 0; ev_status[e] = PV_EV_BAD_OFFSETS; }
+    return;
+  }
+  int K = warp_find_seeds(hist + static_cast<size_t>(e) * C.nbins, nullptr, C, &S, cap, pc_lo, pc_hi);
+  int Ks = K < cap ? K : cap;
+  for (int k = lane; k < Ks; k += 32) {
+    size_t q = static_cast<size_t>(e) * kMaxSeeds + k;
+    seed_lo[q] = S.lo[k];
+    seed_hi[q] = S.hi[k];
+    seed_bin[q] = S.bin[k];
+    seed_z[q] = S.z[k];
+  }
+  if (lane == 0) { seed_n[e] = Ks; ev_status[e] = K > cap ? PV_EV_SEED_OVERFLOW : 0; }
+}
+
+__global__ void __launch_bounds__(256)
+plain_assoc_kernel(Consts C, TrackPtrs T, OutPtrs O, const int32_t* center, int32_t* cid,
+                   const int32_t* seed_n, const int32_t* seed_lo, const int32_t* seed_hi,
+                   const int32_t* seed_bin, const float* seed_z, const int32_t* ev_status) {
+  __shared__ SeedOut S;
+  __shared__ int alive[kMaxSeeds], part[kMaxSeeds], cnt[kMaxSeeds], flag;
+  const int e = blockIdx.x;
+  const int64_t b0 = T.off[e], b1 = T.off[e + 1];
+  const int tid = threadIdx.x;
+  if (offsets_bad(b0, b1, T.n_tracks)) {
+    if (tid == 0) {
+      O.n_per_event[e] = 0;
+      if (O.event_status) O.event_status[e] = PV_EV_BAD_OFFSETS;
+    }
+    return;
+  }
+  const int n = static_cast<int>(b1 - b0);
+  const int K = seed_n[e];
+  if (tid < K) {
+    size_t q = static_cast<size_t>(e) * kMaxSeeds + tid;
+    S.lo[tid] = seed_lo[q];
+    S.hi[tid] = seed_hi[q];
+    S.bin[tid] = seed_bin[q];
+    float zs = seed_z[q];
+    S.z[tid] = zs;
+    S.x[tid] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
+    S.y[tid] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
+  }
+  __syncthreads();
+  int Ka = block_associate(center + b0, cid + b0, n, &S, K, C, alive, part, cnt, &flag);
+  for (int t = tid; t < n; t += blockDim.x) O.track_vertex[b0 + t] = cid[b0 + t];
+  if (tid == 0) {
+    O.n_per_event[e] = Ka;
+    if (O.event_status) O.event_status[e] = ev_status[e];
+  }
+  if (tid < Ka) {
+    size_t q = static_cast<size_t>(e) * O.cap + tid;
+    O.x[q] = S.x[tid];
+    O.y[q] = S.y[tid];
+    O.z[q] = S.z[tid];
+    if (O.bin_lo) O.bin_lo[q] = S.lo[tid];
+    if (O.bin_hi) O.bin_hi[q] = S.hi[tid];
+    if (O.bin_max) O.bin_max[q] = S.bin[tid];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+plain_fit_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, int32_t* cid, int32_t* slot,
+                 float4* A, float2* W) {
+  __shared__ SeedOut S;
+  __shared__ int cnt[kMaxSeeds], voff[kMaxSeeds], base[kMaxSeeds];
+  const int e = blockIdx.x;
+  const int64_t b0 = T.off[e], b1 = T.off[e + 1];
+  const int tid = threadIdx.x;
+  if (offsets_bad(b0, b1, T.n_tracks)) return;
+  const int n = static_cast<int>(b1 - b0);
+  int K = SP.n_per_event[e];
+  const int capk = SP.cap < kMaxSeeds ? SP.cap : kMaxSeeds;
+  K = K < 0 ? 0 : (K > capk ? capk : K);
+  if (tid < K) {
+    size_t q = static_cast<size_t>(e) * SP.cap + tid;
+    S.x[tid] = SP.x[q];
+    S.y[tid] = SP.y[q];
+    S.z[tid] = SP.z[q];
+    cnt[tid] = 0;
+  }
+  __syncthreads();
+  int32_t* c_e = cid + b0;
+  for (int t = tid; t < n; t += blockDim.x) {
+    int c = SP.track_vertex[b0 + t];
+    c = (c >= 0 && c < K) ? c : -1;
+    c_e[t] = c;
+    if (c >= 0) atomicAdd(cnt + c, 1);
+    if (O.track_vertex != SP.track_vertex) O.track_vertex[b0 + t] = c;
+  }
+  if (tid == 0 && O.n_per_event != SP.n_per_event) O.n_per_event[e] = K;
+  __syncthreads();
+  if (tid < 32) warp_offsets(cnt, K, voff, base);
+  __syncthreads();
+  if (tid < 32) warp_slots(c_e, n, base, slot + b0);
+  __syncthreads();
+  block_fit_inputs(T, b0, n, c_e, slot + b0, &S, A + b0, W + b0);
+  __syncthreads();
+  block_fit_event(C, &S, K, voff, cnt, A + b0, W + b0, O, e);
+}
+
+static int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 65535 * 16) g = 65535 * 16;
+  return static_cast<int>(g);
+}
+
+cudaError_t launch_extrapolate(const Consts& C, const TrackPtrs& T, float* zpoca, float* sigma,
+                               int32_t* center, cudaStream_t st) {
+  if (T.n_tracks == 0) return cudaSuccess;
+  plain_extrapolate_kernel<<<grid_for(T.n_tracks, 256), 256, 0, st>>>(C, T, zpoca, sigma, center,
+                                                                      nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_histogram(const Consts& C, const TrackPtrs& T, uint32_t* hist,
+                             const PlainScratch& ws, cudaStream_t st, int* n_launches) {
+  cudaError_t err = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)T.n_events * C.nbins, st);
+  if (err != cudaSuccess) return err;
+  if (T.n_tracks > 0) {
+    plain_extrapolate_kernel<<<grid_for(T.n_tracks, 256), 256, 0, st>>>(
+        C, T, ws.zpoca, ws.sigma, ws.center, ws.j0, ws.j1);
+    ++*n_launches;
+  }
+  plain_hist_kernel<<<T.n_events, 256, 0, st>>>(C, T, ws.zpoca, ws.sigma, ws.center, ws.j0, ws.j1,
+                                                 hist);
+  ++*n_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_find(const Consts& C, const TrackPtrs& T, const OutPtrs& O,
+                              const PlainScratch& ws, cudaStream_t st, int* n_launches) {
+  cudaError_t err = launch_histogram(C, T, ws.hist, ws, st, n_launches);
+  if (err != cudaSuccess) return err;
+  plain_peaks_kernel<<<T.n_events, 32, 0, st>>>(C, T, ws.hist, O.cap, ws.seed_n, ws.seed_lo,
+                                                ws.seed_hi, ws.seed_bin, ws.seed_z, ws.ev_status);
+  plain_assoc_kernel<<<T.n_events, 256, 0, st>>>(C, T, O, ws.center, ws.cid, ws.seed_n, ws.seed_lo,
+                                                 ws.seed_hi, ws.seed_bin, ws.seed_z, ws.ev_status);
+  *n_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
+                             const OutPtrs& O, const PlainScratch& ws, cudaStream_t st,
+                             int* n_launches) {
+  plain_fit_kernel<<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A, ws.W);
+  ++*n_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace pvk

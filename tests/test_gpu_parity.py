@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Bit-exact for z_poca, sigma_poca, histogram bins, seeds,
+cluster bounds and track assignment; within 0.1 um (x, y), 0.5 um (z) and 1e-4
+relative covariance for the fit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_14966_gb300 import synthetic
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pv():
+    import paper_2412_14966_gb300 as pv
+    from paper_2412_14966_gb300 import build
+    build.build()
+    return pv
+
+
+@pytest.fixture(scope="module")
+def ctx(pv):
+    c = pv.Context(device=0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synthetic.workload_small()
+
+
+def _tight(pv, batch, seeds_np, found_ref, beam=(0.0, 0.0, 0.0, 0.0), **cfg):
+    """Both sides refitted from the same seeds to full convergence."""
+    import torch
+    kw = dict(dz_tol=1e-5, dchi2_tol=1e-4, max_iter=60)
+    ctx = pv.Context(device=0, beamline=beam, **cfg, **kw)
+    tracks = pv.Tracks.from_batch(batch)
+    seeds = pv.Vertices({k: torch.from_numpy(v).cuda() for k, v in seeds_np.items()}, 64)
+    out = ctx.fit_batch(tracks, seeds)
+    torch.cuda.synchronize()
+    g = out.numpy()
+    ctx.close()
+    p = G.oracle_params_for(beam=beam, **kw)
+    r = oracle.fit_batch(batch, found_ref, p)
+    return g, r
+
+
+def test_extrapolation_bit_exact(ctx, pv, small):
+    import torch
+    tracks = pv.Tracks.from_batch(small)
+    zp, sg, cb = ctx.extrapolate_batch(tracks)
+    torch.cuda.synchronize()
+    ref = oracle.prepare_f32(small.tracks, oracle.default_params())
+    assert np.array_equal(zp.cpu().numpy().view(np.int32), ref["zpoca"].view(np.int32))
+    fin = np.isfinite(ref["sigma"])
+    assert np.array_equal(sg.cpu().numpy()[fin].view(np.int32), ref["sigma"][fin].view(np.int32))
+    assert np.array_equal(cb.cpu().numpy(), np.where(ref["filled"] > 0, ref["center"], -1))
+
+
+def test_histogram_bit_exact(ctx, pv, small):
+    import torch
+    tracks = pv.Tracks.from_batch(small)
+    h = ctx.histogram_batch(tracks)
+    torch.cuda.synchronize()
+    ref = oracle.find_batch(small, oracle.default_params(), want_hist=True)
+    assert np.array_equal(h.cpu().numpy().view(np.uint32), ref["hist"])
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_find_and_fit_small_workload(ctx, pv, small, fused):
+    s, v = G.gpu_find_fit(ctx, small, fused=fused)
+    p = oracle.default_params()
+    ref = oracle.find_batch(small, p)
+    G.assert_find_equal(s, ref, small)
+    fit = oracle.fit_batch(small, ref, p)
+    worst, nd = G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, small, s, ref))
+    print("worst", worst, "iteration mismatches", nd)
+
+
+def test_plain_path_equals_fused(pv, small):
+    import torch
+    a = pv.Context(device=0)
+    b = pv.Context(device=0, path=pv.PATH_PLAIN)
+    sa, va = G.gpu_find_fit(a, small)
+    sb, vb = G.gpu_find_fit(b, small)
+    E = small.n_events
+    assert np.array_equal(sa["n_per_event"][:E], sb["n_per_event"][:E])
+    assert np.array_equal(sa["track_vertex"][:small.n_tracks], sb["track_vertex"][:small.n_tracks])
+    for e in range(E):
+        n = sa["n_per_event"][e]
+        for k in ("x", "y", "z", "bin_lo", "bin_hi", "bin_max"):
+            assert np.array_equal(sa[k][e, :n], sb[k][e, :n]), (e, k)
+        for k in ("x", "y", "z", "cov", "chi2", "ndof", "n_tracks", "n_iter", "status"):
+            assert np.array_equal(va[k][e, :n], vb[k][e, :n]), (e, k)
+    a.close(); b.close()
+    torch.cuda.synchronize()
+
+
+def test_nominal_workload_full_size_sampled(ctx, pv):
+    """10,000 events at the benchmark's launch configuration; the oracle checks
+    a random sample of events one by one, properties are checked on all."""
+    batch = synthetic.workload_nominal()
+    s, v = G.gpu_find_fit(ctx, batch)
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(batch.n_events, 300, replace=False))
+    sub = batch.subset(sample)
+    p = oracle.default_params()
+    ref = oracle.find_batch(sub, p)
+    # map the sample's rows out of the full result
+    sg = {k: s[k][sample] for k in ("x", "y", "z", "bin_lo", "bin_hi", "bin_max")}
+    sg["n_per_event"] = s["n_per_event"][sample]
+    sg["event_status"] = s["event_status"][sample]
+    idx = synthetic._ranges(batch.offsets[sample], batch.event_sizes()[sample])
+    sg["track_vertex"] = s["track_vertex"][idx]
+    G.assert_find_equal(sg, ref, sub)
+    fit = oracle.fit_batch(sub, ref, p)
+    vg = {k: v[k][sample] for k in ("x", "y", "z", "cov", "n_iter", "status", "n_tracks")}
+    G.assert_fit_close(vg, fit, ref["n"], lambda: _tight(pv, sub, {
+        k: s[k][sample] for k in ("x", "y", "z", "n_per_event")} | {"track_vertex": sg["track_vertex"]}, ref))
+    # properties on all events
+    n = s["n_per_event"][:batch.n_events]
+    assert n.min() >= 0 and n.max() <= 64
+    tv = s["track_vertex"][:batch.n_tracks]
+    ev = np.repeat(np.arange(batch.n_events), batch.event_sizes())
+    assert np.all(tv < n[ev])
+    for e in range(0, batch.n_events, 97):
+        z = s["z"][e, :n[e]]
+        assert np.all(np.diff(z) > 0)
+        assert np.all(np.isfinite(v["z"][e, :n[e]]))
+
+
+def test_mixture_with_fixed_target_sampled(ctx, pv):
+    """Uneven events and the p-gas region (Table smog-pp)."""
+    batch = synthetic.workload_mixture(n_events=3000)
+    s, v = G.gpu_find_fit(ctx, batch)
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(batch.n_events, 300, replace=False))
+    sub = batch.subset(sample)
+    p = oracle.default_params()
+    ref = oracle.find_batch(sub, p)
+    idx = synthetic._ranges(batch.offsets[sample], batch.event_sizes()[sample])
+    sg = {k: s[k][sample] for k in ("x", "y", "z", "bin_lo", "bin_hi", "bin_max", "n_per_event",
+                                    "event_status")}
+    sg["track_vertex"] = s["track_vertex"][idx]
+    G.assert_find_equal(sg, ref, sub)
+    assert (ref["z"][ref["n"] > 0] < -300).any()
+    fit = oracle.fit_batch(sub, ref, p)
+    vg = {k: v[k][sample] for k in ("x", "y", "z", "cov", "n_iter", "status", "n_tracks")}
+    G.assert_fit_close(vg, fit, ref["n"], lambda: _tight(pv, sub, {
+        k: s[k][sample] for k in ("x", "y", "z", "n_per_event")} | {"track_vertex": sg["track_vertex"]}, ref))
+
+
+def test_high_pileup_events(ctx, pv):
+    """~1,200 tracks per event (global-scratch path), overlapping vertices."""
+    batch = synthetic.generate(24, 3, mu=40.0, mean_tracks=28.0, name="pileup-24")
+    s, v = G.gpu_find_fit(ctx, batch)
+    p = oracle.default_params()
+    ref = oracle.find_batch(batch, p)
+    G.assert_find_equal(s, ref, batch)
+    fit = oracle.fit_batch(batch, ref, p)
+    G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref))
+
+
+@pytest.mark.parametrize("beam", [(0.35, -0.2, 1.5e-3, -0.8e-3), (1.092, 0.472, 0.0, 0.0)])
+def test_displaced_and_tilted_beamline(pv, beam):
+    """Nonzero beam position and slope exercise the beam terms of Eq. zpocadef
+    (reading R1) and the seed position on the beamline."""
+    batch = synthetic.workload_small(n_events=60, seed=5)
+    ctx = pv.Context(device=0, beamline=beam)
+    s, v = G.gpu_find_fit(ctx, batch)
+    p = G.oracle_params_for(beam=beam)
+    ref = oracle.find_batch(batch, p)
+    G.assert_find_equal(s, ref, batch)
+    fit = oracle.fit_batch(batch, ref, p)
+    G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref, beam=beam))
+    ctx.close()
+
+
+def test_kahan_accumulation_within_tolerance(pv, small):
+    ctx = pv.Context(device=0, accum_mode=pv.ACCUM_KAHAN)
+    s, v = G.gpu_find_fit(ctx, small)
+    p = oracle.default_params()
+    ref = oracle.find_batch(small, p)
+    G.assert_find_equal(s, ref, small)
+    fit = oracle.fit_batch(small, ref, p)
+    G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, small, s, ref,
+                                                        accum_mode=pv.ACCUM_KAHAN))
+    ctx.close()
+
+
+def test_deterministic_and_alone_equals_mix(ctx, pv):
+    """Per-event results do not depend on the rest of the batch or on
+    scheduling: bit-identical alone and in the mix, run after run."""
+    batch = synthetic.workload_mixture(n_events=800, seed=9)
+    s1, v1 = G.gpu_find_fit(ctx, batch)
+    s2, v2 = G.gpu_find_fit(ctx, batch)
+    for k in ("x", "y", "z", "cov", "status", "n_iter"):
+        for e in range(batch.n_events):
+            n = v1["n_per_event"][e]
+            assert np.array_equal(v1[k][e, :n], v2[k][e, :n]), (k, e)
+    pick = np.array([5, 17, 400, 401, 799, 3])
+    sub = batch.subset(pick)
+    s3, v3 = G.gpu_find_fit(ctx, sub)
+    for i, e in enumerate(pick):
+        n = v1["n_per_event"][e]
+        assert v3["n_per_event"][i] == n
+        for k in ("x", "y", "z", "cov", "chi2", "status", "n_iter"):
+            assert np.array_equal(v3[k][i, :n], v1[k][e, :n]), (k, e)
+
+
+def test_edge_cases(ctx, pv):
+    import torch
+    rng = np.random.default_rng(4)
+    ev = []
+    ev.append(synthetic.straight_tracks((0.0, 0.0, 1.0), [(0.1, 0.0)], [2.0]))          # 1 track
+    ev.append({k: np.zeros(0, np.float32) for k in synthetic.TRACK_FIELDS})            # empty
+    # 100 well separated vertices of 5 tracks: more seeds than the capacity
+    many = [synthetic.straight_tracks((0.0, 0.0, -240.0 + 4.5 * i),
+                                      rng.uniform(-0.3, 0.3, (5, 2)),
+                                      -240.0 + 4.5 * i + rng.uniform(-5, 5, 5), cov_xx=4e-4)
+            for i in range(100)]
+    ev.append({k: np.concatenate([m[k] for m in many]) for k in synthetic.TRACK_FIELDS})
+    # NaN / parallel / out-of-range tracks mixed into a normal event
+    base = synthetic.workload_small(n_events=1, seed=8)
+    t = {k: v.copy() for k, v in base.tracks.items()}
+    t["x"][0] = np.nan
+    t["tx"][1] = 0.0; t["ty"][1] = 0.0
+    t["z"][2] = 1e6
+    t["cyy"][3] = np.inf
+    ev.append(t)
+    # one event of 5,000 tracks
+    big = synthetic.generate(1, 77, mu=170.0, mean_tracks=28.0)
+    ev.append({k: v for k, v in big.tracks.items()})
+    batch = synthetic.batch_from_events(ev)
+    s, v = G.gpu_find_fit(ctx, batch)
+    p = oracle.default_params()
+    ref = oracle.find_batch(batch, p)
+    assert ref["event_status"][2] & oracle.EV_SEED_OVERFLOW
+    G.assert_find_equal(s, ref, batch)
+    fit = oracle.fit_batch(batch, ref, p)
+    G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref))
+    # empty batch
+    empty = synthetic.batch_from_events([])
+    tr = pv.Tracks.from_batch(empty)
+    ctx.fit_batch(tr)
+    torch.cuda.synchronize()
+
+
+def test_bad_offsets_flagged(ctx, pv):
+    import torch
+    batch = synthetic.workload_small(n_events=4, seed=2)
+    tracks = pv.Tracks.from_batch(batch)
+    offs = batch.offsets.copy()
+    offs[2] = offs[1] - 1          # event 1 ends before it starts; event 2 starts earlier
+    bad = pv.Tracks(tracks.cols, torch.from_numpy(offs).cuda())
+    out = ctx.fit_batch(bad)
+    torch.cuda.synchronize()
+    o = out.numpy()
+    assert o["event_status"][1] == pv.EV_BAD_OFFSETS and o["n_per_event"][1] == 0
+    assert o["event_status"][0] != pv.EV_BAD_OFFSETS
+
+
+def test_run_host_equals_device_path(ctx, pv, small):
+    import torch
+    s, v = G.gpu_find_fit(ctx, small)
+    host = pv.Tracks.from_host(small)
+    out = pv.Vertices.empty(small.n_events, small.n_tracks, host=True, pinned=True)
+    ctx.run_host(host, out)
+    o = out.numpy()
+    for e in range(small.n_events):
+        n = v["n_per_event"][e]
+        for k in ("x", "y", "z", "cov", "status", "n_iter"):
+            assert np.array_equal(o[k][e, :n], v[k][e, :n]), (k, e)
+    assert np.array_equal(o["track_vertex"][:small.n_tracks], v["track_vertex"][:small.n_tracks])

@@ -256,3 +256,18 @@ def test_final_selection():
     # gas region: no beamline cut, 3 tracks suffice
     assert fit_at((1.0, 0.0, -400.0), 3)["status"] & oracle.ACCEPTED
     assert fit_at((1.0, 0.0, -400.0), 2)["status"] & oracle.REJ_NTRK
+
+
+def test_tracks_with_non_finite_variance_are_not_used():
+    """Reading R10: a track enters the fit only with finite, positive
+    extrapolated variances; otherwise the fit is that of the other tracks."""
+    rng = np.random.default_rng(19)
+    t = _toy_vertex(rng, 12, (0.0, 0.0, 3.0))
+    p = oracle.default_params()
+    ref = oracle.fit_tracks({k: v[1:] for k, v in t.items()}, (0.0, 0.0, 3.02), p)
+    for field, val in (("cyy", np.inf), ("cxx", np.nan), ("cxx", -1.0)):
+        bad = {k: v.copy() for k, v in t.items()}
+        bad[field][0] = val
+        r = oracle.fit_tracks(bad, (0.0, 0.0, 3.02), p)
+        np.testing.assert_allclose(r["x"], ref["x"], atol=1e-12)
+        assert r["n_tracks"] == ref["n_tracks"]
