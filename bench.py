@@ -201,11 +201,17 @@ def run_reference(args):
     oracle.build()
     batch = synthetic.workload_nominal()
     p = oracle.default_params()
-    # one step = a bounded sample of the workload, so K + W steps end in minutes
-    per_step = min(batch.n_events, 2000)
+    # one step = a bounded sample of the workload, sized from a probe so that
+    # the whole --steps K --warmup W run stays within about two minutes
+    probe = batch.subset(np.arange(50))
+    t0 = time.perf_counter()
+    oracle.find_fit(probe, p)
+    per_event = (time.perf_counter() - t0) / 50
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    per_step = int(max(1, min(batch.n_events, budget / per_event)))
     sub = batch.subset(np.arange(per_step))
     for _ in range(args.warmup):
-        oracle.find_fit(sub.subset(np.arange(min(50, per_step))), p)
+        oracle.find_fit(sub, p)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.find_fit(sub, p)
