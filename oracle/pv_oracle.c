@@ -34,6 +34,10 @@
  *      contents, rounded once to binary32; delta = 0 when 2N_i - N_+ - N_- <= 0.
  *   R10 the fit uses a track only if its state is finite and both variances
  *      extrapolated to the seed z are finite and positive.
+ *   R11 the normal matrix counts as singular when a Gauss-Jordan pivot is not
+ *      above OC_PIVOT_REL times its diagonal element (for example a single
+ *      weighted track, or tracks that are all parallel): the vertex gets the
+ *      SINGULAR status instead of a step along an undetermined direction.
  */
 #include <math.h>
 #include <stdint.h>
@@ -42,6 +46,7 @@
 
 #define OC_ONE 4096          /* histogram weight of one track, R3 */
 #define OC_S_MIN 1e-6f       /* profile half-width below which a track fills one bin */
+#define OC_PIVOT_REL 1e-4    /* relative pivot below which M is singular, R11 */
 
 enum {
   OC_CONVERGED = 1, OC_MAXITER = 2, OC_SINGULAR = 4,
@@ -380,7 +385,8 @@ typedef struct {
 } oc_vertex;
 
 /* Inverse of a symmetric positive definite 3x3 matrix by Gauss-Jordan
- * elimination of [A | I].  Returns 0 if a pivot is not positive and finite. */
+ * elimination of [A | I].  Returns 0 if a pivot is not above OC_PIVOT_REL
+ * times its diagonal element of A, or not finite (R11). */
 static int oc_inverse3(const double A[3][3], double Ainv[3][3]) {
   double a[3][6];
   for (int r = 0; r < 3; ++r)
@@ -388,7 +394,7 @@ static int oc_inverse3(const double A[3][3], double Ainv[3][3]) {
       a[r][c] = (c < 3) ? A[r][c] : (c - 3 == r ? 1.0 : 0.0);
   for (int c = 0; c < 3; ++c) {
     double piv = a[c][c];
-    if (!(piv > 0.0) || !isfinite(piv)) return 0;
+    if (!(piv > 0.0) || !isfinite(piv) || !(piv > OC_PIVOT_REL * A[c][c])) return 0;
     for (int k = 0; k < 6; ++k) a[c][k] /= piv;
     for (int r = 0; r < 3; ++r) {
       if (r == c) continue;

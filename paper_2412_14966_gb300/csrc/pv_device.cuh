@@ -24,6 +24,7 @@ constexpr int kTileWords = kMaxTiles / 32;
 constexpr float kSqrt5 = 2.23606797749979f;   // half-width of the profile in sigma units
 constexpr float kSMin = 1e-6f;                // narrower profiles fill a single bin
 constexpr int kGroup = 8;                     // lanes that fit one vertex
+constexpr float kPivotRel = 1e-4f;            // z pivot below this share of M_zz: singular
 constexpr int kGroupsPerWarp = 32 / kGroup;
 
 // Derived settings, passed by value to every kernel.
@@ -570,7 +571,7 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
         ux = sxz * ix;
         uy = syz * iy;
         s_ = szz - sxz * ux - syz * uy;      // Schur complement: the z pivot
-        ok = s_ > 0.f && isfinite(s_);
+        ok = s_ > kPivotRel * szz && isfinite(s_);
       }
       if (!ok) {
         status = PV_ST_SINGULAR;

@@ -271,3 +271,24 @@ def test_tracks_with_non_finite_variance_are_not_used():
         r = oracle.fit_tracks(bad, (0.0, 0.0, 3.02), p)
         np.testing.assert_allclose(r["x"], ref["x"], atol=1e-12)
         assert r["n_tracks"] == ref["n_tracks"]
+
+
+def test_degenerate_normal_matrix_is_singular():
+    """Reading R11: one weighted track, or tracks sharing one direction, leave
+    the vertex position along the track undetermined: SINGULAR at the first
+    iteration instead of a step along the null direction."""
+    p = oracle.default_params()
+    one = synthetic.straight_tracks((0.0, 0.0, 5.0), [(0.1, -0.05)], [6.0], cov_xx=1e-3)
+    r = oracle.fit_tracks(one, (0.0, 0.0, 5.01), p)
+    assert r["status"] & oracle.SINGULAR and r["n_iter"] == 1
+    par = synthetic.straight_tracks((0.0, 0.0, 5.0), [(0.1, -0.05)] * 4, [6.0, 7.0, 3.0, 4.0],
+                                    cov_xx=1e-3)
+    par["x"] = (par["x"] + np.float32([0.0, 0.01, -0.01, 0.02])).astype(np.float32)
+    r = oracle.fit_tracks(par, (0.0, 0.0, 5.01), p)
+    assert r["status"] & oracle.SINGULAR
+    # two tracks at a clear angle are enough
+    two = synthetic.straight_tracks((0.0, 0.0, 5.0), [(0.1, -0.05), (-0.2, 0.1)], [6.0, 7.0],
+                                    cov_xx=1e-3)
+    r = oracle.fit_tracks(two, (0.0, 0.0, 5.01), p)
+    assert not (r["status"] & oracle.SINGULAR)
+    np.testing.assert_allclose(r["x"], [0.0, 0.0, 5.0], atol=1e-5)
