@@ -291,12 +291,12 @@ int check_tracks(const pv_tracks* t) {
   return PV_OK;
 }
 
-int check_out(const pv_vertices* o, int64_t n_tracks, bool need_xyz) {
+int check_out(const pv_vertices* o, const pv_tracks* t, bool need_xyz) {
   if (!o) return PV_ERR_ARG;
   if (o->capacity < 1 || o->capacity > PV_MAX_SEEDS) return PV_ERR_ARG;
-  if (!o->n_per_event) return PV_ERR_ARG;
-  if (n_tracks > 0 && !o->track_vertex) return PV_ERR_ARG;
-  if (need_xyz && (!o->x || !o->y || !o->z)) return PV_ERR_ARG;
+  if (t->n_events > 0 && !o->n_per_event) return PV_ERR_ARG;
+  if (t->n_tracks > 0 && !o->track_vertex) return PV_ERR_ARG;
+  if (t->n_events > 0 && need_xyz && (!o->x || !o->y || !o->z)) return PV_ERR_ARG;
   return PV_OK;
 }
 
@@ -533,7 +533,7 @@ int pv_find_batch(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* seeds_out, 
   if (!ctx) return PV_ERR_ARG;
   int rc = check_tracks(tracks);
   if (rc != PV_OK) return rc;
-  rc = check_out(seeds_out, tracks->n_tracks, true);
+  rc = check_out(seeds_out, tracks, true);
   if (rc != PV_OK) return rc;
   cudaSetDevice(ctx->device);
   return run_find_or_fit(ctx, tracks, nullptr, seeds_out, static_cast<cudaStream_t>(stream),
@@ -545,10 +545,10 @@ int pv_fit_batch(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
   if (!ctx) return PV_ERR_ARG;
   int rc = check_tracks(tracks);
   if (rc != PV_OK) return rc;
-  rc = check_out(out, tracks->n_tracks, true);
+  rc = check_out(out, tracks, true);
   if (rc != PV_OK) return rc;
   if (seeds) {
-    rc = check_out(seeds, tracks->n_tracks, true);
+    rc = check_out(seeds, tracks, true);
     if (rc != PV_OK) return rc;
   }
   cudaSetDevice(ctx->device);
@@ -588,7 +588,7 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
   if (!ctx) return PV_ERR_ARG;
   int rc = check_tracks(h);
   if (rc != PV_OK) return rc;
-  rc = check_out(ho, h->n_tracks, true);
+  rc = check_out(ho, h, true);
   if (rc != PV_OK) return rc;
   cudaSetDevice(ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -665,7 +665,7 @@ int pv_submit(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, uint64_t* 
   if (!ctx || !ticket) return PV_ERR_ARG;
   int rc = check_tracks(tracks);
   if (rc != PV_OK) return rc;
-  rc = check_out(out, tracks->n_tracks, true);
+  rc = check_out(out, tracks, true);
   if (rc != PV_OK) return rc;
   cudaSetDevice(ctx->device);
   std::lock_guard<std::mutex> g(ctx->mu);
