@@ -242,6 +242,11 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
   if (!(cfg.min_integral_pp >= 0.0f) || !(cfg.min_integral_gas >= 0.0f)) return PV_ERR_ARG;
   C->z_min = cfg.z_min;
   C->dz = cfg.dz;
+  {
+    int ex = 0;
+    float mant = std::frexp(cfg.dz, &ex);
+    C->inv_dz = (mant == 0.5f) ? std::ldexp(1.0f, 1 - ex) : 0.0f;   // dz = 2^(ex-1)
+  }
   C->z_gas = cfg.z_gas;
   C->sig_max_pp = cfg.sigma_max_pp;
   C->sig_max_gas = cfg.sigma_max_gas;

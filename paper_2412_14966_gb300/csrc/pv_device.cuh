@@ -30,6 +30,7 @@ constexpr int kGroupsPerWarp = 32 / kGroup;
 // Derived settings, passed by value to every kernel.
 struct Consts {
   float z_min, dz, z_gas;
+  float inv_dz;             // 1/dz when dz is a power of two (exact), else 0
   float sig_max_pp, sig_max_gas;
   float x_b, y_b, tx_b, ty_b;
   float chi2_max, inv_chi2_max, dchi2_tol, dz_tol, max_r_beam;
@@ -47,7 +48,10 @@ struct Consts {
 
 // Bin of v: floor((v - z_min) / dz); -1 below the range, nbins above it.
 __device__ __forceinline__ int bin_of(float v, const Consts& C) {
-  float q = __fdiv_rn(__fsub_rn(v, C.z_min), C.dz);
+  // dividing by a power of two and multiplying by its exact reciprocal give
+  // the same correctly rounded result
+  float diff = __fsub_rn(v, C.z_min);
+  float q = C.inv_dz != 0.0f ? __fmul_rn(diff, C.inv_dz) : __fdiv_rn(diff, C.dz);
   if (!(q >= 0.0f)) return -1;
   if (q >= __int2float_rn(C.nbins)) return C.nbins;
   return static_cast<int>(q);
@@ -486,19 +490,40 @@ __device__ __forceinline__ float group_sum_c(CSum v) {
 // (shuffles); lanes of groups without a vertex pass cntk = -1.  Track s of the
 // vertex (s = 0 .. cntk-1, in track-index order) is handled by lane s mod 8 of
 // the group.  The result lands in *out on every lane of the group.
+//
+// Each iteration solves the normal equations in sheared coordinates
+// x' = x - c_x z, y' = y - c_y z, with c the weighted mean slope of the
+// vertex's tracks (weights W for the first iteration, w W of the previous
+// iteration afterwards).  The equations keep their structure (the sums use
+// t - c instead of t) and the z pivot s = M_zz - M_xz^2/M_xx - M_yz^2/M_yy,
+// which the shear leaves unchanged, no longer cancels in binary32 when the
+// weighted tracks are nearly parallel.  Step and covariance are mapped back
+// with T = [[1,0,c_x],[0,1,c_y],[0,0,1]] (x = x' + c_x z, C = T C' T^T).
 template <bool kKahan>
 __device__ void group_fit(const float4* A, const float2* W, int cntk, const Consts& C,
                           VertexOut* out) {
   const int r = threadIdx.x & (kGroup - 1);
-  float ax = 0.f, ay = 0.f, az = 0.f;
+  // first shear: W-weighted mean slope of the usable tracks
+  float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+  for (int s = r; s < cntk; s += kGroup) {
+    float4 a = A[s];
+    float2 w2 = W[s];
+    if (!(w2.x > 0.0f)) continue;
+    m0 += w2.x; m1 += w2.x * a.z; m2 += w2.y; m3 += w2.y * a.w;
+  }
+  m0 = group_sum(m0); m1 = group_sum(m1); m2 = group_sum(m2); m3 = group_sum(m3);
+  float cx = m0 > 0.f ? m1 / m0 : 0.f;
+  float cy = m2 > 0.f ? m3 / m2 : 0.f;
+  float ax = 0.f, ay = 0.f, az = 0.f;   // relative to the seed
   bool done = cntk < 0;
   int status = 0, n_iter = 0;
-  float Sxx = 0, Syy = 0, Sxz = 0, Syz = 0, c2sum = 0, sw = 0, dchi2 = 0;
+  float c2sum = 0, sw = 0, dchi2 = 0;
   float ix = 0, iy = 0, ux = 0, uy = 0, is = 0;
   int nw = 0;
   for (int it = 1; it <= C.max_iter; ++it) {
     float v[10];
     int cnt_w = 0;
+    const float axp = ax - cx * az, ayp = ay - cy * az;   // sheared position
     if (kKahan) {
       CSum acc[10];
 #pragma unroll
@@ -508,18 +533,19 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
           float4 a = A[s];
           float2 w2 = W[s];
           if (!(w2.x > 0.0f)) continue;
-          float rx = a.x + az * a.z - ax;
-          float ry = a.y + az * a.w - ay;
+          float dtx = a.z - cx, dty = a.w - cy;
+          float rx = a.x + az * dtx - axp;
+          float ry = a.y + az * dty - ayp;
           float c2 = rx * rx * w2.x + ry * ry * w2.y;
           float w = 0.f;
           if (c2 < C.chi2_max) { float f = 1.0f - c2 * C.inv_chi2_max; w = f * f; }
           if (w > 0.f) {
             float wx = w * w2.x, wy = w * w2.y;
             acc[0].add(wx); acc[1].add(wy);
-            acc[2].add(wx * a.z); acc[3].add(wy * a.w);
-            acc[4].add(wx * a.z * a.z + wy * a.w * a.w);
+            acc[2].add(wx * dtx); acc[3].add(wy * dty);
+            acc[4].add(wx * dtx * dtx + wy * dty * dty);
             acc[5].add(wx * rx); acc[6].add(wy * ry);
-            acc[7].add(wx * a.z * rx + wy * a.w * ry);
+            acc[7].add(wx * dtx * rx + wy * dty * ry);
             acc[8].add(w * c2); acc[9].add(w);
             ++cnt_w;
           }
@@ -535,18 +561,19 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
           float4 a = A[s];
           float2 w2 = W[s];
           if (!(w2.x > 0.0f)) continue;
-          float rx = a.x + az * a.z - ax;
-          float ry = a.y + az * a.w - ay;
+          float dtx = a.z - cx, dty = a.w - cy;
+          float rx = a.x + az * dtx - axp;
+          float ry = a.y + az * dty - ayp;
           float c2 = rx * rx * w2.x + ry * ry * w2.y;
           float w = 0.f;
           if (c2 < C.chi2_max) { float f = 1.0f - c2 * C.inv_chi2_max; w = f * f; }
           if (w > 0.f) {
             float wx = w * w2.x, wy = w * w2.y;
             v[0] += wx; v[1] += wy;
-            v[2] += wx * a.z; v[3] += wy * a.w;
-            v[4] += wx * a.z * a.z + wy * a.w * a.w;
+            v[2] += wx * dtx; v[3] += wy * dty;
+            v[4] += wx * dtx * dtx + wy * dty * dty;
             v[5] += wx * rx; v[6] += wy * ry;
-            v[7] += wx * a.z * rx + wy * a.w * ry;
+            v[7] += wx * dtx * rx + wy * dty * ry;
             v[8] += w * c2; v[9] += w;
             ++cnt_w;
           }
@@ -557,11 +584,10 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
     }
     cnt_w = group_sum_i(cnt_w);
     if (!done) {
-      // M = [[Sxx,0,-Sxz],[0,Syy,-Syz],[-Sxz,-Syz,Szz]], g = (-bx, -by, bz)
+      // sheared M = [[Sxx,0,-Sxz],[0,Syy,-Syz],[-Sxz,-Syz,Szz]], rhs (bx, by, -bz)
       float sxx = v[0], syy = v[1], sxz = v[2], syz = v[3], szz = v[4];
       float bx = v[5], by = v[6], bz = v[7];
       n_iter = it;
-      Sxx = sxx; Syy = syy; Sxz = sxz; Syz = syz;
       c2sum = v[8]; sw = v[9]; nw = cnt_w;
       float s_ = 0.f;
       bool ok = sxx > 0.f && syy > 0.f && isfinite(sxx) && isfinite(syy);
@@ -571,7 +597,9 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
         ux = sxz * ix;
         uy = syz * iy;
         s_ = szz - sxz * ux - syz * uy;      // Schur complement: the z pivot
-        ok = s_ > kPivotRel * szz && isfinite(s_);
+        // M_zz of the unsheared matrix, for the relative pivot test
+        float mzz = szz + 2.0f * (cx * sxz + cy * syz) + cx * cx * sxx + cy * cy * syy;
+        ok = s_ > kPivotRel * mzz && isfinite(s_);
       }
       if (!ok) {
         status = PV_ST_SINGULAR;
@@ -583,9 +611,15 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
         float dx = (bx + sxz * dz) * ix;
         float dy = (by + syz * dz) * iy;
         dchi2 = -bx * dx - by * dy + bz * dz;
-        ax += dx;
-        ay += dy;
+        ax += dx + cx * dz;
+        ay += dy + cy * dz;
         az += dz;
+        // covariance terms in the unsheared frame; the next shear is the
+        // w W-weighted mean slope of this iteration, ux + c_x
+        ux += cx;
+        uy += cy;
+        cx = ux;
+        cy = uy;
         if (fabsf(dchi2) < C.dchi2_tol && fabsf(dz) < C.dz_tol) {
           status = PV_ST_CONVERGED;
           done = true;
@@ -597,15 +631,17 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
     if (__all_sync(0xffffffffu, done)) break;
   }
   if (cntk < 0) return;
+  // C = T C' T^T with ux, uy already mapped back (M_xz/M_xx of the unsheared M)
+  const float uxo = ux, uyo = uy;
   out->x = ax;       // relative to the seed; the caller adds the seed position
   out->y = ay;
   out->z = az;
-  out->cov[0] = ix + ux * ux * is;   // xx
-  out->cov[1] = ux * uy * is;        // xy
-  out->cov[2] = iy + uy * uy * is;   // yy
-  out->cov[3] = ux * is;             // xz
-  out->cov[4] = uy * is;             // yz
-  out->cov[5] = is;                  // zz
+  out->cov[0] = ix + uxo * uxo * is;   // xx
+  out->cov[1] = uxo * uyo * is;        // xy
+  out->cov[2] = iy + uyo * uyo * is;   // yy
+  out->cov[3] = uxo * is;              // xz
+  out->cov[4] = uyo * is;              // yz
+  out->cov[5] = is;                    // zz
   out->chi2 = c2sum + dchi2;
   out->ndof = 2.0f * sw - 3.0f;
   out->n_tracks = nw;

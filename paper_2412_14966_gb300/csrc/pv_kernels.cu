@@ -101,6 +101,7 @@ __device__ __forceinline__ void warp_slots(const int* cid, int n, int* base, int
 
 // Fit every vertex of one event (block-cooperative).  A, W: per-track fit
 // inputs in vertex order; voff/cnt: vertex ranges.
+template <bool kKahan>
 __device__ void block_fit_event(const Consts& C, const SeedOut* S, int Ka, const int* voff,
                                 const int* cnt, const float4* A, const float2* W,
                                 const OutPtrs& O, int e) {
@@ -113,10 +114,7 @@ __device__ void block_fit_event(const Consts& C, const SeedOut* S, int Ka, const
     int cntk = has ? cnt[k] : -1;
     int o = has ? voff[k] : 0;
     VertexOut v;
-    if (C.accum_mode == PV_ACCUM_KAHAN)
-      group_fit<true>(A + o, W + o, cntk, C, &v);
-    else
-      group_fit<false>(A + o, W + o, cntk, C, &v);
+    group_fit<kKahan>(A + o, W + o, cntk, C, &v);
     if (has && (lane & 7) == 0) {
       size_t q = static_cast<size_t>(e) * O.cap + k;
       float x = S->x[k] + v.x, y = S->y[k] + v.y, z = S->z[k] + v.z;
@@ -158,7 +156,7 @@ __device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tr
 // ---------------------------------------------------------------------------
 // fused persistent kernel
 
-template <int MODE>
+template <int MODE, bool kKahan>
 __global__ void __launch_bounds__(kFusedThreads)
 fused_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G, int* work_counter) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -294,35 +292,44 @@ fused_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G, int*
       __syncthreads();
       block_fit_inputs(T, b0, n, cid, slot, S, A, W);
       __syncthreads();
-      block_fit_event(C, S, Ka, voff, cnt, A, W, O, e);
+      block_fit_event<kKahan>(C, S, Ka, voff, cnt, A, W, O, e);
     }
   }
 }
 
-int fused_blocks_per_sm(int nbins, int mode) {
-  int blocks = 0;
-  size_t sm = fused_smem_bytes(nbins, mode);
-  cudaError_t err;
-  if (mode == kFind)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<kFind>, kFusedThreads, sm);
-  else if (mode == kFit)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<kFit>, kFusedThreads, sm);
-  else
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<kFindFit>, kFusedThreads, sm);
-  if (err != cudaSuccess) return 0;
-  return blocks;
+template <int MODE, bool K>
+static cudaError_t setup_one(int nbins) {
+  cudaError_t err = cudaFuncSetAttribute(fused_kernel<MODE, K>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fused_smem_bytes(nbins, MODE));
+  if (err != cudaSuccess) return err;
+  return cudaFuncSetAttribute(fused_kernel<MODE, K>,
+                              cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
 }
 
 cudaError_t fused_setup(int nbins) {
   cudaError_t err;
-  err = cudaFuncSetAttribute(fused_kernel<kFind>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fused_smem_bytes(nbins, kFind));
-  if (err != cudaSuccess) return err;
-  err = cudaFuncSetAttribute(fused_kernel<kFit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fused_smem_bytes(nbins, kFit));
-  if (err != cudaSuccess) return err;
-  return cudaFuncSetAttribute(fused_kernel<kFindFit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)fused_smem_bytes(nbins, kFindFit));
+  if ((err = setup_one<kFind, false>(nbins)) != cudaSuccess) return err;
+  if ((err = setup_one<kFit, false>(nbins)) != cudaSuccess) return err;
+  if ((err = setup_one<kFit, true>(nbins)) != cudaSuccess) return err;
+  if ((err = setup_one<kFindFit, false>(nbins)) != cudaSuccess) return err;
+  return setup_one<kFindFit, true>(nbins);
+}
+
+template <int MODE, bool K>
+static int blocks_one(int nbins) {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<MODE, K>, kFusedThreads,
+                                                    fused_smem_bytes(nbins, MODE)) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+int fused_blocks_per_sm(int nbins, int mode) {
+  if (mode == kFind) return blocks_one<kFind, false>(nbins);
+  if (mode == kFit) return blocks_one<kFit, false>(nbins);
+  return blocks_one<kFindFit, false>(nbins);
 }
 
 cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
@@ -331,12 +338,17 @@ cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const Se
   size_t sm = fused_smem_bytes(C.nbins, mode);
   cudaError_t err = cudaMemsetAsync(work_counter, 0, sizeof(int), st);
   if (err != cudaSuccess) return err;
+  const bool kahan = C.accum_mode == PV_ACCUM_KAHAN;
   if (mode == kFind)
-    fused_kernel<kFind><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+    fused_kernel<kFind, false><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+  else if (mode == kFit && kahan)
+    fused_kernel<kFit, true><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
   else if (mode == kFit)
-    fused_kernel<kFit><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+    fused_kernel<kFit, false><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+  else if (kahan)
+    fused_kernel<kFindFit, true><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
   else
-    fused_kernel<kFindFit><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+    fused_kernel<kFindFit, false><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
   return cudaGetLastError();
 }
 
@@ -439,6 +451,7 @@ plain_assoc_kernel(Consts C, TrackPtrs T, OutPtrs O, const int32_t* center, int3
   }
 }
 
+template <bool kKahan>
 __global__ void __launch_bounds__(256)
 plain_fit_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, int32_t* cid, int32_t* slot,
                  float4* A, float2* W) {
@@ -476,7 +489,7 @@ plain_fit_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, int32_t* cid, in
   __syncthreads();
   block_fit_inputs(T, b0, n, c_e, slot + b0, &S, A + b0, W + b0);
   __syncthreads();
-  block_fit_event(C, &S, K, voff, cnt, A + b0, W + b0, O, e);
+  block_fit_event<kKahan>(C, &S, K, voff, cnt, A + b0, W + b0, O, e);
 }
 
 static int grid_for(int64_t n, int threads) {
@@ -524,7 +537,10 @@ cudaError_t launch_plain_find(const Consts& C, const TrackPtrs& T, const OutPtrs
 cudaError_t launch_plain_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
                              const OutPtrs& O, const PlainScratch& ws, cudaStream_t st,
                              int* n_launches) {
-  plain_fit_kernel<<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A, ws.W);
+  if (C.accum_mode == PV_ACCUM_KAHAN)
+    plain_fit_kernel<true><<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A, ws.W);
+  else
+    plain_fit_kernel<false><<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A, ws.W);
   ++*n_launches;
   return cudaGetLastError();
 }
