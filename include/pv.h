@@ -193,6 +193,23 @@ int pv_poll(pv_ctx* ctx, uint64_t ticket, int* done);
  * unknown or not yet done. */
 int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns);
 
+/* Steps (a)-(d3) as one fused pass, like pv_fit_batch with seeds == NULL,
+ * but without allocating device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while
+ * they run (cudaMalloc / cudaFree may synchronise the whole device, which a
+ * real-time loop cannot afford; some applications give all device memory to
+ * their own allocator and run with a fixed budget).  Its scratch is a static
+ * device array of 8 MiB in the library, held by every GPU that loads the
+ * library until the process exits; batches needing more scratch (more than
+ * about 233,000 tracks) are refused with PV_ERR_CAPACITY and a message in
+ * pv_last_cuda_error.  The first call on a device looks the array up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array, so calls whose work overlaps on the GPU race:
+ * run them on one stream or order them with events.  tracks and out are
+ * device memory as for pv_fit_batch; the context's path setting is ignored
+ * (always the fused kernel).  Asynchronous on cuda_stream. */
+int pv_find_fit_static(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, void* cuda_stream);
+
 /* Human-readable name of an error code. */
 const char* pv_strerror(int code);
 

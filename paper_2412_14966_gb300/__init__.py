@@ -32,6 +32,7 @@ EXPORTED = (
     "pv_config_default", "pv_init", "pv_destroy", "pv_find_batch", "pv_fit_batch",
     "pv_extrapolate_batch", "pv_histogram_batch", "pv_num_bins", "pv_run_host", "pv_submit",
     "pv_poll", "pv_request_latency_ns", "pv_strerror", "pv_last_cuda_error", "pv_launch_count",
+    "pv_find_fit_static",
 )
 
 
@@ -118,6 +119,7 @@ def load():
     L.pv_last_cuda_error.restype = C.c_char_p
     L.pv_launch_count.argtypes = [C.c_void_p]
     L.pv_launch_count.restype = C.c_uint64
+    L.pv_find_fit_static.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
     _LIB = L
     return L
 
@@ -309,6 +311,18 @@ class Context:
         self._check(self.lib.pv_histogram_batch(self.h, C.byref(t), _ptr(h), _stream_handle(stream)),
                     "pv_histogram_batch")
         return h[:tracks.n_events]
+
+    def find_fit_static(self, tracks: Tracks, out: Vertices | None = None,
+                        stream=None) -> Vertices:
+        """``pv_find_fit_static``: the fused find + fit with the library's
+        static device scratch instead of allocated memory, for callers that
+        cannot allocate device memory while they run.  Batches up to about
+        233,000 tracks; overlapping calls race (they share the scratch)."""
+        out = out or Vertices.empty(tracks.n_events, tracks.n_tracks)
+        t, o = tracks.struct(), out.struct()
+        self._check(self.lib.pv_find_fit_static(self.h, C.byref(t), C.byref(o),
+                                                _stream_handle(stream)), "pv_find_fit_static")
+        return out
 
     # -- host entry point -----------------------------------------------------
     def run_host(self, tracks: Tracks, out: Vertices, stream=None) -> Vertices:

@@ -747,3 +747,71 @@ const char* pv_last_cuda_error(const pv_ctx* ctx) { return ctx ? ctx->last_error
 uint64_t pv_launch_count(const pv_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free variant of the fused find + fit.
+//
+// Some callers cannot allocate device memory once they are running: a
+// real-time loop cannot afford cudaMalloc / cudaFree, which may synchronise
+// the whole device, and an application that hands all device memory to its
+// own allocator at start-up runs with a fixed budget.  pv_find_fit_static
+// serves them: its scratch (the work counter and the per-track arrays of
+// events above 256 tracks) lives in the file-scope array below, which every
+// GPU that loads this library holds until the process exits.  Host code only
+// ever passes the array's device address, obtained with cudaGetSymbolAddress
+// once per device (the array's name is a host-side stand-in, not a device
+// address).  Calls share the array: two calls whose work overlaps on the GPU
+// race, so callers serialise them (one stream, or events between streams).
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;   // 8 MiB
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (set-up on first use).
+int static_scratch_for(pv_ctx* ctx, void** out) {
+  if (ctx->device < 0 || ctx->device >= kStaticMaxDevices) return PV_ERR_ARG;
+  std::lock_guard<std::mutex> g(g_static_mu);
+  if (!g_static_ptr[ctx->device]) {
+    void* p = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (err != cudaSuccess || !p) return fail_cuda(ctx, err == cudaSuccess ? cudaErrorUnknown : err);
+    g_static_ptr[ctx->device] = p;
+  }
+  *out = g_static_ptr[ctx->device];
+  return PV_OK;
+}
+
+}  // namespace
+
+extern "C" int pv_find_fit_static(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out,
+                                  void* stream) {
+  if (!ctx) return PV_ERR_ARG;
+  int rc = check_tracks(tracks);
+  if (rc != PV_OK) return rc;
+  rc = check_out(out, tracks, true);
+  if (rc != PV_OK) return rc;
+  FusedLayout L(tracks->n_tracks);
+  if (L.total > kStaticScratchBytes) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "pv_find_fit_static: %lld tracks need %zu bytes of scratch; the static "
+                  "buffer holds %zu bytes", static_cast<long long>(tracks->n_tracks), L.total,
+                  kStaticScratchBytes);
+    ctx->last_error = msg;
+    return PV_ERR_CAPACITY;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return PV_ERR_CUDA;
+  void* base = nullptr;
+  rc = static_scratch_for(ctx, &base);
+  if (rc != PV_OK) return rc;
+  if (tracks->n_events == 0) return PV_OK;
+  // enqueue_fused clears the work counter on the stream before the kernel
+  return enqueue_fused(ctx, pvk::kFindFit, tracks, nullptr, out, base,
+                       static_cast<cudaStream_t>(stream));
+}
