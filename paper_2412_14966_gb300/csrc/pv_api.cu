@@ -58,10 +58,12 @@ struct DevBuf {
 
 size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
-// Carves fused-path scratch for n_tracks tracks out of one buffer.
+// Carves fused-path scratch for a batch out of one buffer.
 struct FusedLayout {
-  size_t counter, center, cid, slot, A, W, total;
-  explicit FusedLayout(int64_t n) {
+  size_t counter, center, cid, slot, A, W, work, total;
+  int64_t work_cap;
+  FusedLayout(int64_t n, int64_t n_events, int cap) {
+    work_cap = n_events * static_cast<int64_t>(cap < PV_MAX_SEEDS ? cap : PV_MAX_SEEDS);
     size_t o = 0;
     counter = o; o += 256;
     A = o; o += round16(sizeof(float4) * n);
@@ -69,6 +71,7 @@ struct FusedLayout {
     center = o; o += round16(sizeof(int32_t) * n);
     cid = o; o += round16(sizeof(int32_t) * n);
     slot = o; o += round16(sizeof(int32_t) * n);
+    work = o; o += round16(sizeof(pvk::VertexWork) * work_cap);
     total = o;
   }
   pvk::TrackScratch scratch(void* base) const {
@@ -79,10 +82,10 @@ struct FusedLayout {
     s.slot = reinterpret_cast<int32_t*>(b + slot);
     s.A = reinterpret_cast<float4*>(b + A);
     s.W = reinterpret_cast<float2*>(b + W);
+    s.work = reinterpret_cast<pvk::VertexWork*>(b + work);
+    s.work_cap = static_cast<int>(work_cap);
+    s.counters = reinterpret_cast<int*>(b + counter);
     return s;
-  }
-  int* work_counter(void* base) const {
-    return reinterpret_cast<int*>(static_cast<char*>(base) + counter);
   }
 };
 
@@ -197,7 +200,8 @@ struct pv_ctx {
   pv_beamline beam{};
   Consts C{};
   int n_sm = 0;
-  int fused_grid[4] = {0, 0, 0, 0};   // by mode
+  int fused_grid[4] = {0, 0, 0, 0};   // find kernel, by mode
+  int fit_grid[2] = {0, 0};           // fit kernel: binary32, compensated
   DevBuf fused_ws, plain_ws;
   // host-buffer entry point staging
   DevBuf host_in, host_out;
@@ -337,15 +341,18 @@ pvk::SeedPtrs seed_ptrs(const pv_vertices* s) {
   return S;
 }
 
-// Enqueue the fused kernel with scratch at `base` (laid out by FusedLayout).
+// Enqueue the fused kernels with scratch at `base` (laid out by FusedLayout).
 int enqueue_fused(pv_ctx* ctx, int mode, const pv_tracks* tracks, const pv_vertices* seeds,
                   const pv_vertices* out, void* base, cudaStream_t st) {
-  FusedLayout L(tracks->n_tracks);
+  FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
   int grid = ctx->fused_grid[mode];
   if (grid < 1) grid = ctx->n_sm;
+  int fit_grid = ctx->fit_grid[ctx->C.accum_mode == PV_ACCUM_KAHAN ? 1 : 0];
+  if (fit_grid < 1) fit_grid = ctx->n_sm;
+  int n = 0;
   PV_CUDA(ctx, pvk::launch_fused(mode, ctx->C, track_ptrs(tracks), seed_ptrs(seeds),
-                                 out_ptrs(out), L.scratch(base), L.work_counter(base), grid, st));
-  ctx->launches += 1;
+                                 out_ptrs(out), L.scratch(base), grid, fit_grid, st, &n));
+  ctx->launches += n;
   return PV_OK;
 }
 
@@ -368,14 +375,16 @@ int run_find_or_fit(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* see
     ctx->launches += n;
     return PV_OK;
   }
-  FusedLayout L(tracks->n_tracks);
+  FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
   PV_CUDA(ctx, ctx->fused_ws.ensure(L.total));
   return enqueue_fused(ctx, mode, tracks, seeds, out, ctx->fused_ws.p, st);
 }
 
 // ---- serving internals (ctx->mu held) ------------------------------------
 
-size_t request_bytes(const pv_tracks* t) { return FusedLayout(t->n_tracks).total; }
+size_t request_bytes(const pv_tracks* t, const pv_vertices* o) {
+  return FusedLayout(t->n_tracks, t->n_events, o->capacity).total;
+}
 
 void CUDART_CB on_request_done(void* arg) {
   Request* r = static_cast<Request*>(arg);
@@ -491,6 +500,10 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
   for (int mode = 1; mode <= 3; ++mode) {
     int per_sm = pvk::fused_blocks_per_sm(C.nbins, mode);
     ctx->fused_grid[mode] = ctx->n_sm * (per_sm > 0 ? per_sm : 1);
+  }
+  for (int k = 0; k < 2; ++k) {
+    int per_sm = pvk::fit_blocks_per_sm(k == 1);
+    ctx->fit_grid[k] = ctx->n_sm * (per_sm > 0 ? per_sm : 1);
   }
   *out = ctx;
   return PV_OK;
@@ -676,7 +689,7 @@ int pv_submit(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, uint64_t* 
   std::lock_guard<std::mutex> g(ctx->mu);
   rc = ensure_pool(ctx);
   if (rc != PV_OK) return rc;
-  size_t bytes = (request_bytes(tracks) + 255) / 256 * 256;
+  size_t bytes = (request_bytes(tracks, out) + 255) / 256 * 256;
   if (bytes > ctx->arena.size) return PV_ERR_NOMEM;
   if (ctx->pending.size() >= kMaxQueued) {
     rc = pump(ctx);
@@ -796,13 +809,13 @@ extern "C" int pv_find_fit_static(pv_ctx* ctx, const pv_tracks* tracks, pv_verti
   if (rc != PV_OK) return rc;
   rc = check_out(out, tracks, true);
   if (rc != PV_OK) return rc;
-  FusedLayout L(tracks->n_tracks);
+  FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
   if (L.total > kStaticScratchBytes) {
     char msg[160];
     std::snprintf(msg, sizeof(msg),
-                  "pv_find_fit_static: %lld tracks need %zu bytes of scratch; the static "
-                  "buffer holds %zu bytes", static_cast<long long>(tracks->n_tracks), L.total,
-                  kStaticScratchBytes);
+                  "pv_find_fit_static: %lld tracks in %d events need %zu bytes of scratch; "
+                  "the static buffer holds %zu bytes", static_cast<long long>(tracks->n_tracks),
+                  tracks->n_events, L.total, kStaticScratchBytes);
     ctx->last_error = msg;
     return PV_ERR_CAPACITY;
   }
@@ -811,7 +824,7 @@ extern "C" int pv_find_fit_static(pv_ctx* ctx, const pv_tracks* tracks, pv_verti
   rc = static_scratch_for(ctx, &base);
   if (rc != PV_OK) return rc;
   if (tracks->n_events == 0) return PV_OK;
-  // enqueue_fused clears the work counter on the stream before the kernel
+  // enqueue_fused clears the work counters on the stream before the kernels
   return enqueue_fused(ctx, pvk::kFindFit, tracks, nullptr, out, base,
                        static_cast<cudaStream_t>(stream));
 }

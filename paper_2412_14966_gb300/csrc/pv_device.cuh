@@ -155,9 +155,8 @@ struct SeedOut {   // shared-memory seed table of one event
 // running maximum of the open piece (L) and the next maximum (R) if both the
 // piece [s, m] and the rest [m+1, b] hold the minimal integral.
 template <class Emit>
-__device__ void split_walk(const uint32_t* N, int a, int b, const Consts& C, Emit&& emit) {
-  uint64_t total = 0;
-  for (int i = a; i <= b; ++i) total += N[i];
+__device__ void split_walk(const uint32_t* N, int a, int b, uint64_t total, const Consts& C,
+                           Emit&& emit) {
   int s = a;
   uint64_t pre_s = 0;                 // sum over [a, s)
   int top = a;
@@ -244,13 +243,19 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
   auto process = [&](int count) {
     // lane j walks proto-cluster n_done + j (pass 1 counts kept pieces)
     int a = 0, b = -1;
+    uint64_t total = 0;
     if (lane < count) {
       a = pc_lo[(n_done + lane) & 127];
       b = pc_hi[(n_done + lane) & 127];
+      for (int i = a; i <= b; ++i) total += N[i];
     }
+    // no piece of a proto-cluster can hold more than its total integral, so
+    // one below the smaller threshold yields no seed: skip its walk
+    const uint64_t t_min = C.t_pp < C.t_gas ? C.t_pp : C.t_gas;
+    const bool walk = lane < count && total >= t_min;
     int kept = 0;
-    if (lane < count) {
-      split_walk(N, a, b, C, [&](int lo, int hi, uint64_t integral) {
+    if (walk) {
+      split_walk(N, a, b, total, C, [&](int lo, int hi, uint64_t integral) {
         int im;
         if (keep_piece(N, lo, hi, integral, C, &im)) ++kept;
       });
@@ -260,10 +265,10 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
       int v = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += v;
     }
-    int total = __shfl_sync(0xffffffffu, incl, 31);
+    int n_kept = __shfl_sync(0xffffffffu, incl, 31);
     int pos = n_seeds + incl - kept;
-    if (lane < count && kept > 0 && pos < cap) {
-      split_walk(N, a, b, C, [&](int lo, int hi, uint64_t integral) {
+    if (walk && kept > 0 && pos < cap) {
+      split_walk(N, a, b, total, C, [&](int lo, int hi, uint64_t integral) {
         int im;
         if (keep_piece(N, lo, hi, integral, C, &im)) {
           if (pos < cap) {
@@ -279,7 +284,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
         }
       });
     }
-    n_seeds += total;
+    n_seeds += n_kept;
     n_done += count;
     __syncwarp();
   };

@@ -1,12 +1,15 @@
 // pv_kernels.cu -- sm_103a kernels of the primary-vertex library.
 //
-// Fused path: one persistent kernel, one event at a time per CTA, events taken
-// from a global work counter (uneven event sizes balance themselves).  Per
-// event the CTA keeps the z histogram in shared memory (cleared only where
+// Fused path: two persistent kernels.  The find kernel takes one event at a
+// time per CTA from a global work counter (uneven event sizes balance
+// themselves), keeps the z histogram in shared memory (cleared only where
 // tracks wrote, tracked by a 32-bin tile mask), finds seeds with warp ballots,
-// associates tracks, and fits all vertices with 8-lane groups.  Per-track
-// state stays in shared memory for events up to kSmallCap tracks and in an
-// L2-resident global scratch for larger events, so no event size is refused.
+// associates tracks, and writes each track's fit inputs, in vertex order, to
+// an L2-resident scratch with one work item per vertex.  The fit kernel then
+// fits vertices of all events, one 8-lane group per vertex, at high
+// occupancy.  Per-track association state stays in shared memory for events
+// up to kSmallCap tracks and in global scratch for larger events, so no event
+// size is refused.
 //
 // Plain path: one kernel per step (extrapolate / histogram / peaks /
 // associate / fit), one CTA per event, histograms and per-track state in
@@ -18,11 +21,11 @@ namespace pvk {
 using namespace pvdev;
 
 // ---------------------------------------------------------------------------
-// shared-memory layout of the fused kernel
+// shared-memory layout of the find kernel
 
 struct Layout {
-  size_t A, W, hist, tmask, seeds, pc_lo, pc_hi, alive, part, cnt, voff, base, center, cid, slot,
-      misc, total;
+  size_t hist, tmask, seeds, pc_lo, pc_hi, alive, part, cnt, voff, base, center, cid, slot, misc,
+      total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -30,11 +33,8 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 __host__ __device__ inline Layout make_layout(int nbins, int mode) {
   Layout L;
   size_t o = 0;
-  const bool fit = (mode & kFit) != 0;
   const bool find = (mode & kFind) != 0;
   const int ntiles = (nbins + 31) / 32;
-  L.A = o;      o += fit ? sizeof(float4) * kSmallCap : 0;
-  L.W = o;      o += fit ? sizeof(float2) * kSmallCap : 0;
   L.hist = o;   o += find ? sizeof(uint32_t) * ntiles * 32 : 0;
   L.tmask = o;  o += sizeof(uint32_t) * kTileWords;
   L.seeds = o;  o += align_up(sizeof(SeedOut), 16);
@@ -99,8 +99,29 @@ __device__ __forceinline__ void warp_slots(const int* cid, int n, int* base, int
   }
 }
 
-// Fit every vertex of one event (block-cooperative).  A, W: per-track fit
-// inputs in vertex order; voff/cnt: vertex ranges.
+// Write the fit of vertex k of event e (result relative to the seed at
+// (xs, ys, zs)) with its selection status.
+__device__ __forceinline__ void write_vertex(const Consts& C, const OutPtrs& O, int e, int k,
+                                             float xs, float ys, float zs, const VertexOut& v) {
+  size_t q = static_cast<size_t>(e) * O.cap + k;
+  float x = xs + v.x, y = ys + v.y, z = zs + v.z;
+  int st = select_vertex(x, y, z, v.n_tracks, v.status, C);
+  O.x[q] = x;
+  O.y[q] = y;
+  O.z[q] = z;
+  if (O.cov) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) O.cov[q * 6 + c] = v.cov[c];
+  }
+  if (O.chi2) O.chi2[q] = v.chi2;
+  if (O.ndof) O.ndof[q] = v.ndof;
+  if (O.n_tracks) O.n_tracks[q] = v.n_tracks;
+  if (O.n_iter) O.n_iter[q] = v.n_iter;
+  if (O.status) O.status[q] = st;
+}
+
+// Fit every vertex of one event (block-cooperative; used by the plain path).
+// A, W: per-track fit inputs in vertex order; voff/cnt: vertex ranges.
 template <bool kKahan>
 __device__ void block_fit_event(const Consts& C, const SeedOut* S, int Ka, const int* voff,
                                 const int* cnt, const float4* A, const float2* W,
@@ -115,23 +136,7 @@ __device__ void block_fit_event(const Consts& C, const SeedOut* S, int Ka, const
     int o = has ? voff[k] : 0;
     VertexOut v;
     group_fit<kKahan>(A + o, W + o, cntk, C, &v);
-    if (has && (lane & 7) == 0) {
-      size_t q = static_cast<size_t>(e) * O.cap + k;
-      float x = S->x[k] + v.x, y = S->y[k] + v.y, z = S->z[k] + v.z;
-      int st = select_vertex(x, y, z, v.n_tracks, v.status, C);
-      O.x[q] = x;
-      O.y[q] = y;
-      O.z[q] = z;
-      if (O.cov) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) O.cov[q * 6 + c] = v.cov[c];
-      }
-      if (O.chi2) O.chi2[q] = v.chi2;
-      if (O.ndof) O.ndof[q] = v.ndof;
-      if (O.n_tracks) O.n_tracks[q] = v.n_tracks;
-      if (O.n_iter) O.n_iter[q] = v.n_iter;
-      if (O.status) O.status[q] = st;
-    }
+    if (has && (lane & 7) == 0) write_vertex(C, O, e, k, S->x[k], S->y[k], S->z[k], v);
   }
 }
 
@@ -154,15 +159,19 @@ __device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tr
 }
 
 // ---------------------------------------------------------------------------
-// fused persistent kernel
+// find kernel (fused path, stage 1)
+//
+// kFind:    steps (a)-(d1); outputs seeds and assignments.
+// kFindFit: the same, then fit inputs for every track (global scratch, vertex
+//           order) and one work item per vertex for the fit kernel; the seed
+//           position is left in the output row, which the fit overwrites.
+// kFit:     seeds and assignments from the caller, then fit inputs and work.
 
-template <int MODE, bool kKahan>
+template <int MODE>
 __global__ void __launch_bounds__(kFusedThreads)
-fused_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G, int* work_counter) {
+find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Layout Lo = make_layout(C.nbins, MODE);
-  float4* sA = reinterpret_cast<float4*>(smem + Lo.A);
-  float2* sW = reinterpret_cast<float2*>(smem + Lo.W);
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem + Lo.hist);
   uint32_t* tmask = reinterpret_cast<uint32_t*>(smem + Lo.tmask);
   SeedOut* S = reinterpret_cast<SeedOut*>(smem + Lo.seeds);
@@ -191,7 +200,7 @@ fused_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G, int*
   __syncthreads();
 
   for (int iter = 0;; ++iter) {
-    if (tid == 0) misc[iter & 1] = atomicAdd(work_counter, 1);
+    if (tid == 0) misc[iter & 1] = atomicAdd(G.counters, 1);
     __syncthreads();
     const int e = misc[iter & 1];
     if (e >= T.n_events) break;
@@ -208,8 +217,6 @@ fused_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G, int*
     int* center = small ? s_center : G.center + b0;
     int* cid = small ? s_cid : G.cid + b0;
     int* slot = small ? s_slot : G.slot + b0;
-    float4* A = small ? sA : G.A + b0;
-    float2* W = small ? sW : G.W + b0;
     int Ka = 0;
 
     if (MODE & kFind) {
@@ -254,22 +261,26 @@ fused_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G, int*
         if (O.bin_lo) O.bin_lo[q] = S->lo[tid];
         if (O.bin_hi) O.bin_hi[q] = S->hi[tid];
         if (O.bin_max) O.bin_max[q] = S->bin[tid];
-        if (MODE == kFind) {
-          O.x[q] = S->x[tid];
-          O.y[q] = S->y[tid];
-          O.z[q] = S->z[tid];
-        }
+        O.x[q] = S->x[tid];
+        O.y[q] = S->y[tid];
+        O.z[q] = S->z[tid];
       }
     } else {
       // fit only: seeds and assignment from the caller
       int K = SP.n_per_event[e];
-      const int capk = SP.cap < kMaxSeeds ? SP.cap : kMaxSeeds;
+      int capk = SP.cap < O.cap ? SP.cap : O.cap;
+      capk = capk < kMaxSeeds ? capk : kMaxSeeds;
       K = K < 0 ? 0 : (K > capk ? capk : K);
       if (tid < K) {
         size_t q = static_cast<size_t>(e) * SP.cap + tid;
-        S->x[tid] = SP.x[q];
-        S->y[tid] = SP.y[q];
-        S->z[tid] = SP.z[q];
+        float xs = SP.x[q], ys = SP.y[q], zs = SP.z[q];
+        S->x[tid] = xs;
+        S->y[tid] = ys;
+        S->z[tid] = zs;
+        size_t qo = static_cast<size_t>(e) * O.cap + tid;
+        O.x[qo] = xs;
+        O.y[qo] = ys;
+        O.z[qo] = zs;
         cnt[tid] = 0;
       }
       __syncthreads();
@@ -286,69 +297,117 @@ fused_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G, int*
     }
 
     if (MODE & kFit) {
-      if (warp == 0) warp_offsets(cnt, Ka, voff, base);
+      // fit inputs in vertex order (global scratch) and one work item per vertex
+      if (warp == 0) {
+        warp_offsets(cnt, Ka, voff, base);
+        if (lane == 0) misc[4] = atomicAdd(G.counters + 1, Ka);
+      }
       __syncthreads();
       if (warp == 0) warp_slots(cid, n, base, slot);
+      if (tid < Ka && misc[4] + tid < G.work_cap) {
+        VertexWork w;
+        w.off = b0 + voff[tid];
+        w.e = e;
+        w.kc = tid | (cnt[tid] << 8);
+        G.work[misc[4] + tid] = w;
+      }
       __syncthreads();
-      block_fit_inputs(T, b0, n, cid, slot, S, A, W);
-      __syncthreads();
-      block_fit_event<kKahan>(C, S, Ka, voff, cnt, A, W, O, e);
+      block_fit_inputs(T, b0, n, cid, slot, S, G.A + b0, G.W + b0);
     }
   }
 }
 
-template <int MODE, bool K>
-static cudaError_t setup_one(int nbins) {
-  cudaError_t err = cudaFuncSetAttribute(fused_kernel<MODE, K>,
+// ---------------------------------------------------------------------------
+// vertex fit kernel (fused path, stage 2): every 8-lane group fits one vertex
+// of any event; warps take 4 work items at a time.
+
+template <bool kKahan>
+__global__ void __launch_bounds__(kFitThreads)
+fit_kernel(Consts C, TrackScratch G, OutPtrs O) {
+  const int lane = threadIdx.x & 31;
+  const int n = min(G.counters[1], G.work_cap);
+  for (;;) {
+    int b = 0;
+    if (lane == 0) b = atomicAdd(G.counters + 2, kGroupsPerWarp);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (b >= n) break;
+    const int v = b + (lane >> 3);
+    const bool has = v < n;
+    VertexWork w;
+    w.off = 0; w.e = 0; w.kc = 0;
+    if (has) w = G.work[v];
+    const int k = w.kc & 0xff;
+    const int cntk = has ? (w.kc >> 8) : -1;
+    VertexOut out;
+    group_fit<kKahan>(G.A + w.off, G.W + w.off, cntk, C, &out);
+    if (has && (lane & 7) == 0) {
+      size_t q = static_cast<size_t>(w.e) * O.cap + k;
+      write_vertex(C, O, w.e, k, O.x[q], O.y[q], O.z[q], out);
+    }
+  }
+}
+
+template <int MODE>
+static cudaError_t setup_find(int nbins) {
+  cudaError_t err = cudaFuncSetAttribute(find_kernel<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)fused_smem_bytes(nbins, MODE));
   if (err != cudaSuccess) return err;
-  return cudaFuncSetAttribute(fused_kernel<MODE, K>,
-                              cudaFuncAttributePreferredSharedMemoryCarveout,
+  return cudaFuncSetAttribute(find_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
 }
 
 cudaError_t fused_setup(int nbins) {
   cudaError_t err;
-  if ((err = setup_one<kFind, false>(nbins)) != cudaSuccess) return err;
-  if ((err = setup_one<kFit, false>(nbins)) != cudaSuccess) return err;
-  if ((err = setup_one<kFit, true>(nbins)) != cudaSuccess) return err;
-  if ((err = setup_one<kFindFit, false>(nbins)) != cudaSuccess) return err;
-  return setup_one<kFindFit, true>(nbins);
+  if ((err = setup_find<kFind>(nbins)) != cudaSuccess) return err;
+  if ((err = setup_find<kFit>(nbins)) != cudaSuccess) return err;
+  return setup_find<kFindFit>(nbins);
 }
 
-template <int MODE, bool K>
-static int blocks_one(int nbins) {
+template <int MODE>
+static int find_blocks(int nbins) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<MODE, K>, kFusedThreads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, find_kernel<MODE>, kFusedThreads,
                                                     fused_smem_bytes(nbins, MODE)) != cudaSuccess)
     return 0;
   return blocks;
 }
 
 int fused_blocks_per_sm(int nbins, int mode) {
-  if (mode == kFind) return blocks_one<kFind, false>(nbins);
-  if (mode == kFit) return blocks_one<kFit, false>(nbins);
-  return blocks_one<kFindFit, false>(nbins);
+  if (mode == kFind) return find_blocks<kFind>(nbins);
+  if (mode == kFit) return find_blocks<kFit>(nbins);
+  return find_blocks<kFindFit>(nbins);
+}
+
+int fit_blocks_per_sm(bool kahan) {
+  int blocks = 0;
+  cudaError_t err = kahan ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fit_kernel<true>,
+                                                                          kFitThreads, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fit_kernel<false>,
+                                                                          kFitThreads, 0);
+  return err == cudaSuccess ? blocks : 0;
 }
 
 cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
-                         const OutPtrs& O, const TrackScratch& ws, int* work_counter, int grid,
-                         cudaStream_t st) {
+                         const OutPtrs& O, const TrackScratch& ws, int find_grid, int fit_grid,
+                         cudaStream_t st, int* n_launches) {
   size_t sm = fused_smem_bytes(C.nbins, mode);
-  cudaError_t err = cudaMemsetAsync(work_counter, 0, sizeof(int), st);
+  cudaError_t err = cudaMemsetAsync(ws.counters, 0, 4 * sizeof(int), st);
   if (err != cudaSuccess) return err;
-  const bool kahan = C.accum_mode == PV_ACCUM_KAHAN;
   if (mode == kFind)
-    fused_kernel<kFind, false><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
-  else if (mode == kFit && kahan)
-    fused_kernel<kFit, true><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+    find_kernel<kFind><<<find_grid, kFusedThreads, sm, st>>>(C, T, S, O, ws);
   else if (mode == kFit)
-    fused_kernel<kFit, false><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
-  else if (kahan)
-    fused_kernel<kFindFit, true><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+    find_kernel<kFit><<<find_grid, kFusedThreads, sm, st>>>(C, T, S, O, ws);
   else
-    fused_kernel<kFindFit, false><<<grid, kFusedThreads, sm, st>>>(C, T, S, O, ws, work_counter);
+    find_kernel<kFindFit><<<find_grid, kFusedThreads, sm, st>>>(C, T, S, O, ws);
+  ++*n_launches;
+  if (mode & kFit) {
+    if (C.accum_mode == PV_ACCUM_KAHAN)
+      fit_kernel<true><<<fit_grid, kFitThreads, 0, st>>>(C, ws, O);
+    else
+      fit_kernel<false><<<fit_grid, kFitThreads, 0, st>>>(C, ws, O);
+    ++*n_launches;
+  }
   return cudaGetLastError();
 }
 
@@ -463,7 +522,8 @@ plain_fit_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, int32_t* cid, in
   if (offsets_bad(b0, b1, T.n_tracks)) return;
   const int n = static_cast<int>(b1 - b0);
   int K = SP.n_per_event[e];
-  const int capk = SP.cap < kMaxSeeds ? SP.cap : kMaxSeeds;
+  int capk = SP.cap < O.cap ? SP.cap : O.cap;
+  capk = capk < kMaxSeeds ? capk : kMaxSeeds;
   K = K < 0 ? 0 : (K > capk ? capk : K);
   if (tid < K) {
     size_t q = static_cast<size_t>(e) * SP.cap + tid;

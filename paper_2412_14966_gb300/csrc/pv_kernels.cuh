@@ -32,14 +32,25 @@ struct SeedPtrs {            // seeds read by the fit-only kernel
   int32_t cap;
 };
 
-// Global scratch for per-track state of events larger than the in-shared
-// capacity (indexed by the global track index).
+// One vertex to fit: its tracks' fit inputs are A/W[off .. off + cnt), its
+// results go to row e, column k of the outputs (which hold the seed position
+// until the fit overwrites them).
+struct VertexWork {
+  long long off;
+  int e;
+  int kc;           // k | cnt << 8
+};
+
+// Global scratch of the fused path (indexed by the global track index).
 struct TrackScratch {
-  int32_t* center;
+  int32_t* center;      // per track, events above kSmallCap tracks
   int32_t* cid;
   int32_t* slot;
-  float4* A;
+  float4* A;            // per track: fit inputs in vertex order
   float2* W;
+  VertexWork* work;     // vertex work list
+  int work_cap;         // its capacity: events x vertex capacity per event
+  int* counters;        // [0] next event, [1] vertices listed, [2] next vertex to fit
 };
 
 enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3 };
@@ -70,11 +81,15 @@ struct PlainScratch {
 size_t fused_smem_bytes(int nbins, int mode);
 cudaError_t fused_setup(int nbins);
 
+// Enqueues the fused path: counter reset, find kernel, then (modes with a fit)
+// the vertex fit kernel.  *n_launches receives the kernels enqueued.
 cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, const SeedPtrs& S,
-                         const OutPtrs& O, const TrackScratch& ws, int* work_counter,
-                         int grid, cudaStream_t st);
+                         const OutPtrs& O, const TrackScratch& ws, int find_grid, int fit_grid,
+                         cudaStream_t st, int* n_launches);
 
 int fused_blocks_per_sm(int nbins, int mode);
+int fit_blocks_per_sm(bool kahan);
+constexpr int kFitThreads = 256;
 
 cudaError_t launch_plain_find(const pvdev::Consts& C, const TrackPtrs& T, const OutPtrs& O,
                               const PlainScratch& ws, cudaStream_t st, int* n_launches);

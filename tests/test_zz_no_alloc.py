@@ -35,6 +35,11 @@ def _compare(out: dict, ref: dict, batch):
             assert G.cov_error(out["cov"][e, k], ref["cov"][e, k]) < G.TOL_COV, (e, k)
 
 
+def _scratch_bytes(batch, capacity=64):
+    """Scratch a batch needs: 36 B per track, 16 B per event and vertex slot."""
+    return 256 + 36 * batch.n_tracks + 16 * batch.n_events * capacity
+
+
 def test_static_scratch_entry_point_matches_allocating_one():
     import torch
 
@@ -42,9 +47,10 @@ def test_static_scratch_entry_point_matches_allocating_one():
     from paper_2412_14966_gb300 import build
     build.build()
     ctx = pv.Context(device=0)
-    # ~190k tracks, including events above 256 tracks (they use the scratch arrays)
-    batch = synthetic.workload_nominal(n_events=1200, seed=11)
-    assert batch.n_tracks < 233_000 and (batch.event_sizes() > 256).any()
+    # about 160k tracks, including events above 256 tracks (they use the
+    # per-track scratch arrays); the batch's scratch fits in the 8 MiB array
+    batch = synthetic.workload_nominal(n_events=1000, seed=11)
+    assert _scratch_bytes(batch) <= 8 << 20 and (batch.event_sizes() > 256).any()
     tracks = pv.Tracks.from_batch(batch)
     ref = ctx.fit_batch(tracks)
     torch.cuda.synchronize()
@@ -55,7 +61,7 @@ def test_static_scratch_entry_point_matches_allocating_one():
         _compare(out.numpy(), ref, batch)
     # a batch whose scratch would not fit is refused, not truncated
     big = synthetic.workload_nominal(n_events=1600, seed=12)
-    assert big.n_tracks > 233_008
+    assert _scratch_bytes(big) > 8 << 20
     with pytest.raises(pv.PVError) as err:
         ctx.find_fit_static(pv.Tracks.from_batch(big))
     assert err.value.code == pv.PV_ERR_CAPACITY
