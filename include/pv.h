@@ -200,10 +200,11 @@ int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns);
  * real-time loop cannot afford; some applications give all device memory to
  * their own allocator and run with a fixed budget).  Its scratch is a static
  * device array of 8 MiB in the library, held by every GPU that loads the
- * library until the process exits.  A batch needs 36 bytes per track plus 16
- * bytes per event and vertex slot (out->capacity), so about 190,000 tracks of
- * 160-track events at capacity 64; batches needing more are refused with
- * PV_ERR_CAPACITY and a message in pv_last_cuda_error.  The first call on a device looks the array up
+ * library until the process exits.  A batch needs 40 bytes per track plus 32
+ * bytes per vertex slot, where the slots are the smaller of the track count
+ * and events x out->capacity: about 155,000 tracks of 160-track events at
+ * capacity 64.  Batches needing more are refused with PV_ERR_CAPACITY and a
+ * message in pv_last_cuda_error.  The first call on a device looks the array up
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array, so calls whose work overlaps on the GPU race:
  * run them on one stream or order them with events.  tracks and out are

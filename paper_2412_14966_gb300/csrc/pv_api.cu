@@ -60,10 +60,10 @@ size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
 // Carves fused-path scratch for a batch out of one buffer.
 struct FusedLayout {
-  size_t counter, center, cid, slot, A, W, work, total;
+  size_t counter, center, cid, slot, sorted, A, W, work, total;
   int64_t work_cap;
   FusedLayout(int64_t n, int64_t n_events, int cap) {
-    work_cap = n_events * static_cast<int64_t>(cap < PV_MAX_SEEDS ? cap : PV_MAX_SEEDS);
+    work_cap = pvk::work_capacity(n, n_events, cap);
     size_t o = 0;
     counter = o; o += 256;
     A = o; o += round16(sizeof(float4) * n);
@@ -71,6 +71,7 @@ struct FusedLayout {
     center = o; o += round16(sizeof(int32_t) * n);
     cid = o; o += round16(sizeof(int32_t) * n);
     slot = o; o += round16(sizeof(int32_t) * n);
+    sorted = o; o += round16(sizeof(int32_t) * n);
     work = o; o += round16(sizeof(pvk::VertexWork) * work_cap);
     total = o;
   }
@@ -80,6 +81,7 @@ struct FusedLayout {
     s.center = reinterpret_cast<int32_t*>(b + center);
     s.cid = reinterpret_cast<int32_t*>(b + cid);
     s.slot = reinterpret_cast<int32_t*>(b + slot);
+    s.sorted = reinterpret_cast<int32_t*>(b + sorted);
     s.A = reinterpret_cast<float4*>(b + A);
     s.W = reinterpret_cast<float2*>(b + W);
     s.work = reinterpret_cast<pvk::VertexWork*>(b + work);
@@ -290,6 +292,7 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
 int check_tracks(const pv_tracks* t) {
   if (!t) return PV_ERR_ARG;
   if (t->n_events < 0 || t->n_tracks < 0) return PV_ERR_ARG;
+  if (t->n_tracks > 0x7fffffffLL) return PV_ERR_CAPACITY;   // 32-bit track indices
   if (t->n_events > 0 && !t->event_offsets) return PV_ERR_ARG;
   if (t->n_tracks > 0) {
     const float* p[11] = {t->x, t->y, t->z, t->tx, t->ty, t->cxx, t->cxtx, t->ctxtx,

@@ -148,6 +148,7 @@ __device__ __forceinline__ void fill_profile(uint32_t* hist, float zpoca, float 
 struct SeedOut {   // shared-memory seed table of one event
   int lo[kMaxSeeds], hi[kMaxSeeds], bin[kMaxSeeds];
   float z[kMaxSeeds], x[kMaxSeeds], y[kMaxSeeds];
+  uint32_t nm[kMaxSeeds], ni[kMaxSeeds], np[kMaxSeeds];   // N[bin-1], N[bin], N[bin+1]
 };
 
 // Walk proto-cluster [a, b] of N; calls emit(lo, hi, integral) per piece in
@@ -212,11 +213,10 @@ __device__ __forceinline__ bool keep_piece(const uint32_t* N, int lo, int hi, ui
 }
 
 // z_seed = z_mid(i) + delta dz, delta from the exact bin contents in binary64
-// (Sec. 3.3), rounded once to binary32.
-__device__ __forceinline__ float seed_z(const uint32_t* N, int i, const Consts& C) {
-  long long nm = (i > 0) ? static_cast<long long>(N[i - 1]) : 0;
-  long long np = (i + 1 < C.nbins) ? static_cast<long long>(N[i + 1]) : 0;
-  long long ni = static_cast<long long>(N[i]);
+// (Sec. 3.3), rounded once to binary32.  nm, ni, np = N[i-1], N[i], N[i+1]
+// (0 outside the histogram).
+__device__ __forceinline__ float seed_z_from(long long nm, long long ni, long long np, int i,
+                                             const Consts& C) {
   long long num = np - nm;
   long long den = 2 * ni - np - nm;
   double delta = 0.0;
@@ -228,13 +228,18 @@ __device__ __forceinline__ float seed_z(const uint32_t* N, int i, const Consts& 
   return __double2float_rn(__dadd_rn(zmid, t3));
 }
 
+__device__ __forceinline__ uint32_t bin_or_zero(const uint32_t* N, int j, const Consts& C) {
+  return (j >= 0 && j < C.nbins) ? N[j] : 0u;
+}
+
 // Warp-cooperative peak search over a histogram N (shared or global).  If
 // tmask is non-null only tiles (32 bins) whose bit is set can hold non-zero
 // bins; otherwise every tile is scanned.  pc_lo / pc_hi are a 128-entry ring
 // in shared memory.  Writes up to cap seeds into S in z order and returns the
 // number found (which may exceed cap).  All 32 lanes must call it.
+template <bool kSeedZ>
 __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
-                               SeedOut* S, int cap, int* pc_lo, int* pc_hi) {
+                                      SeedOut* S, int cap, int* pc_lo, int* pc_hi) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int n_seeds = 0;
@@ -272,13 +277,20 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
         int im;
         if (keep_piece(N, lo, hi, integral, C, &im)) {
           if (pos < cap) {
-            float zs = seed_z(N, im, C);
+            const uint32_t nm = bin_or_zero(N, im - 1, C), ni = N[im],
+                           np = bin_or_zero(N, im + 1, C);
             S->lo[pos] = lo;
             S->hi[pos] = hi;
             S->bin[pos] = im;
-            S->z[pos] = zs;
-            S->x[pos] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
-            S->y[pos] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
+            S->nm[pos] = nm;
+            S->ni[pos] = ni;
+            S->np[pos] = np;
+            if (kSeedZ) {
+              float zs = seed_z_from(nm, ni, np, im, C);
+              S->z[pos] = zs;
+              S->x[pos] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
+              S->y[pos] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
+            }
           }
           ++pos;
         }
@@ -389,12 +401,14 @@ __device__ int block_associate(const CenterT* center, CidT* cid, int n, SeedOut*
   if (tid < 32) {
     int lo[2], hi[2], bn[2];
     float z[2], x[2], y[2];
+    uint32_t nm[2], ni[2], np[2];
     for (int h = 0; h < 2; ++h) {
       int q = tid + 32 * h;
       if (q < ka) {
         int k = alive[q];
         lo[h] = S->lo[k]; hi[h] = S->hi[k]; bn[h] = S->bin[k];
         z[h] = S->z[k]; x[h] = S->x[k]; y[h] = S->y[k];
+        nm[h] = S->nm[k]; ni[h] = S->ni[k]; np[h] = S->np[k];
       }
     }
     __syncwarp();
@@ -403,6 +417,7 @@ __device__ int block_associate(const CenterT* center, CidT* cid, int n, SeedOut*
       if (q < ka) {
         S->lo[q] = lo[h]; S->hi[q] = hi[h]; S->bin[q] = bn[h];
         S->z[q] = z[h]; S->x[q] = x[h]; S->y[q] = y[h];
+        S->nm[q] = nm[h]; S->ni[q] = ni[h]; S->np[q] = np[h];
       }
     }
   }

@@ -99,6 +99,20 @@ __device__ __forceinline__ void warp_slots(const int* cid, int n, int* base, int
   }
 }
 
+// What group_fit returns for a vertex without tracks: singular at the first
+// iteration (or unconverged with no iteration when max_iter is 0).
+__device__ __forceinline__ VertexOut empty_fit(const Consts& C) {
+  VertexOut v;
+  v.x = v.y = v.z = 0.f;
+  for (int c = 0; c < 6; ++c) v.cov[c] = 0.f;
+  v.chi2 = 0.f;
+  v.ndof = -3.f;
+  v.n_tracks = 0;
+  v.n_iter = C.max_iter >= 1 ? 1 : 0;
+  v.status = C.max_iter >= 1 ? PV_ST_SINGULAR : PV_ST_MAXITER;
+  return v;
+}
+
 // Write the fit of vertex k of event e (result relative to the seed at
 // (xs, ys, zs)) with its selection status.
 __device__ __forceinline__ void write_vertex(const Consts& C, const OutPtrs& O, int e, int k,
@@ -239,7 +253,9 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       __syncthreads();
       // (c): seeds from the touched tiles (warp 0)
       if (warp == 0) {
-        int K = warp_find_seeds(hist, tmask, C, S, O.cap, pc_lo, pc_hi);
+        // the seed position is computed here only when it is the output;
+        // otherwise the fit kernel derives it from the bins around the maximum
+        int K = warp_find_seeds<MODE == kFind>(hist, tmask, C, S, O.cap, pc_lo, pc_hi);
         if (lane == 0) misc[2] = K;
       }
       __syncthreads();
@@ -261,9 +277,11 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
         if (O.bin_lo) O.bin_lo[q] = S->lo[tid];
         if (O.bin_hi) O.bin_hi[q] = S->hi[tid];
         if (O.bin_max) O.bin_max[q] = S->bin[tid];
-        O.x[q] = S->x[tid];
-        O.y[q] = S->y[tid];
-        O.z[q] = S->z[tid];
+        if (MODE == kFind) {
+          O.x[q] = S->x[tid];
+          O.y[q] = S->y[tid];
+          O.z[q] = S->z[tid];
+        }
       }
     } else {
       // fit only: seeds and assignment from the caller
@@ -273,14 +291,10 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       K = K < 0 ? 0 : (K > capk ? capk : K);
       if (tid < K) {
         size_t q = static_cast<size_t>(e) * SP.cap + tid;
-        float xs = SP.x[q], ys = SP.y[q], zs = SP.z[q];
-        S->x[tid] = xs;
-        S->y[tid] = ys;
-        S->z[tid] = zs;
-        size_t qo = static_cast<size_t>(e) * O.cap + tid;
-        O.x[qo] = xs;
-        O.y[qo] = ys;
-        O.z[qo] = zs;
+        S->x[tid] = SP.x[q];
+        S->y[tid] = SP.y[q];
+        S->z[tid] = SP.z[q];
+        S->bin[tid] = -1;             // the seed is given, not a histogram maximum
         cnt[tid] = 0;
       }
       __syncthreads();
@@ -297,22 +311,59 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
     }
 
     if (MODE & kFit) {
-      // fit inputs in vertex order (global scratch) and one work item per vertex
+      // tracks in vertex order and one work item per vertex with tracks; a
+      // vertex without tracks gets the (singular) result of an empty fit here
+      if (warp == 0) warp_offsets(cnt, Ka, voff, base);
+      __syncthreads();
       if (warp == 0) {
-        warp_offsets(cnt, Ka, voff, base);
-        if (lane == 0) misc[4] = atomicAdd(G.counters + 1, Ka);
+        warp_slots(cid, n, base, slot);
+      } else if (warp == 1) {
+        const unsigned lt = (1u << lane) - 1u;
+        const bool h0 = lane < Ka && cnt[lane] > 0;
+        const bool h1 = lane + 32 < Ka && cnt[lane + 32] > 0;
+        const unsigned m0 = __ballot_sync(0xffffffffu, h0);
+        const unsigned m1 = __ballot_sync(0xffffffffu, h1);
+        int wb = 0;
+        if (lane == 0) wb = atomicAdd(G.counters + 1, __popc(m0) + __popc(m1));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        for (int h = 0; h < 2; ++h) {
+          const int k = lane + 32 * h;
+          if (k >= Ka) continue;
+          const unsigned m = h ? m1 : m0;
+          const int idx = wb + (h ? __popc(m0) : 0) + __popc(m & lt);
+          if (cnt[k] > 0) {
+            if (idx < G.work_cap) {
+              VertexWork w;
+              w.off = static_cast<int>(b0 + voff[k]);
+              w.e = e;
+              w.kc = k | (cnt[k] << 8);
+              w.bin = S->bin[k];
+              if (w.bin >= 0) {
+                w.a = S->nm[k]; w.b = S->ni[k]; w.c = S->np[k];
+              } else {
+                w.a = __float_as_uint(S->x[k]);
+                w.b = __float_as_uint(S->y[k]);
+                w.c = __float_as_uint(S->z[k]);
+              }
+              w.pad = 0;
+              G.work[idx] = w;
+            }
+          } else {
+            float xs = S->x[k], ys = S->y[k], zs = S->z[k];
+            if (S->bin[k] >= 0) {
+              zs = seed_z_from(S->nm[k], S->ni[k], S->np[k], S->bin[k], C);
+              xs = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
+              ys = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
+            }
+            write_vertex(C, O, e, k, xs, ys, zs, empty_fit(C));
+          }
+        }
       }
       __syncthreads();
-      if (warp == 0) warp_slots(cid, n, base, slot);
-      if (tid < Ka && misc[4] + tid < G.work_cap) {
-        VertexWork w;
-        w.off = b0 + voff[tid];
-        w.e = e;
-        w.kc = tid | (cnt[tid] << 8);
-        G.work[misc[4] + tid] = w;
+      for (int t = tid; t < n; t += NT) {
+        const int c = cid[t];
+        if (c >= 0) G.sorted[b0 + slot[t]] = static_cast<int32_t>(b0 + t);
       }
-      __syncthreads();
-      block_fit_inputs(T, b0, n, cid, slot, S, G.A + b0, G.W + b0);
     }
   }
 }
@@ -323,8 +374,9 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
 
 template <bool kKahan>
 __global__ void __launch_bounds__(kFitThreads)
-fit_kernel(Consts C, TrackScratch G, OutPtrs O) {
+fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
   const int lane = threadIdx.x & 31;
+  const int r = lane & (kGroup - 1);
   const int n = min(G.counters[1], G.work_cap);
   for (;;) {
     int b = 0;
@@ -334,16 +386,32 @@ fit_kernel(Consts C, TrackScratch G, OutPtrs O) {
     const int v = b + (lane >> 3);
     const bool has = v < n;
     VertexWork w;
-    w.off = 0; w.e = 0; w.kc = 0;
+    w.off = 0; w.e = 0; w.kc = 0; w.bin = -1; w.a = w.b = w.c = 0u; w.pad = 0;
     if (has) w = G.work[v];
     const int k = w.kc & 0xff;
     const int cntk = has ? (w.kc >> 8) : -1;
-    VertexOut out;
-    group_fit<kKahan>(G.A + w.off, G.W + w.off, cntk, C, &out);
-    if (has && (lane & 7) == 0) {
-      size_t q = static_cast<size_t>(w.e) * O.cap + k;
-      write_vertex(C, O, w.e, k, O.x[q], O.y[q], O.z[q], out);
+    // seed position: given, or z_seed from the bins around the maximum
+    // (binary64, one lane per group) with x, y on the beamline
+    float zs = __uint_as_float(w.c);
+    if (has && w.bin >= 0 && r == 0) zs = seed_z_from(w.a, w.b, w.c, w.bin, C);
+    zs = __shfl_sync(0xffffffffu, zs, lane & ~(kGroup - 1));
+    float xs = __uint_as_float(w.a), ys = __uint_as_float(w.b);
+    if (w.bin >= 0) {
+      xs = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
+      ys = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
     }
+    // this lane's tracks: fit inputs relative to the seed (read back below
+    // by the same lane only)
+    float4* A = G.A + w.off;
+    float2* W = G.W + w.off;
+    for (int s = r; s < cntk; s += kGroup) {
+      const int t = G.sorted[w.off + s];
+      make_fit_track(T.x[t], T.y[t], T.z[t], T.tx[t], T.ty[t], T.cxx[t], T.cxtx[t], T.ctxtx[t],
+                     T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, A + s, W + s);
+    }
+    VertexOut out;
+    group_fit<kKahan>(A, W, cntk, C, &out);
+    if (has && r == 0) write_vertex(C, O, w.e, k, xs, ys, zs, out);
   }
 }
 
@@ -403,9 +471,9 @@ cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const Se
   ++*n_launches;
   if (mode & kFit) {
     if (C.accum_mode == PV_ACCUM_KAHAN)
-      fit_kernel<true><<<fit_grid, kFitThreads, 0, st>>>(C, ws, O);
+      fit_kernel<true><<<fit_grid, kFitThreads, 0, st>>>(C, T, ws, O);
     else
-      fit_kernel<false><<<fit_grid, kFitThreads, 0, st>>>(C, ws, O);
+      fit_kernel<false><<<fit_grid, kFitThreads, 0, st>>>(C, T, ws, O);
     ++*n_launches;
   }
   return cudaGetLastError();
@@ -452,7 +520,8 @@ plain_peaks_kernel(Consts C, TrackPtrs T, const uint32_t* hist, int cap, int32_t
     if (lane == 0) { seed_n[e] = 0; ev_status[e] = PV_EV_BAD_OFFSETS; }
     return;
   }
-  int K = warp_find_seeds(hist + static_cast<size_t>(e) * C.nbins, nullptr, C, &S, cap, pc_lo, pc_hi);
+  int K = warp_find_seeds<true>(hist + static_cast<size_t>(e) * C.nbins, nullptr, C, &S, cap, pc_lo,
+                                pc_hi);
   int Ks = K < cap ? K : cap;
   for (int k = lane; k < Ks; k += 32) {
     size_t q = static_cast<size_t>(e) * kMaxSeeds + k;

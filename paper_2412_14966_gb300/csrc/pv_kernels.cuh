@@ -32,13 +32,17 @@ struct SeedPtrs {            // seeds read by the fit-only kernel
   int32_t cap;
 };
 
-// One vertex to fit: its tracks' fit inputs are A/W[off .. off + cnt), its
-// results go to row e, column k of the outputs (which hold the seed position
-// until the fit overwrites them).
+// One vertex to fit: its tracks are sorted[off .. off + cnt) (global track
+// indices in track-index order) and its results go to row e, column k of the
+// outputs.  bin >= 0: the seed comes from the histogram, a, b, c = N[bin-1],
+// N[bin], N[bin+1]; bin < 0: a, b, c are the bit patterns of the seed's x, y, z.
 struct VertexWork {
-  long long off;
+  int off;
   int e;
   int kc;           // k | cnt << 8
+  int bin;
+  uint32_t a, b, c;
+  int pad;
 };
 
 // Global scratch of the fused path (indexed by the global track index).
@@ -46,6 +50,7 @@ struct TrackScratch {
   int32_t* center;      // per track, events above kSmallCap tracks
   int32_t* cid;
   int32_t* slot;
+  int32_t* sorted;      // per track: global track indices in vertex order
   float4* A;            // per track: fit inputs in vertex order
   float2* W;
   VertexWork* work;     // vertex work list
@@ -86,6 +91,14 @@ cudaError_t fused_setup(int nbins);
 cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, const SeedPtrs& S,
                          const OutPtrs& O, const TrackScratch& ws, int find_grid, int fit_grid,
                          cudaStream_t st, int* n_launches);
+
+// Upper bound of the vertices a batch can list: per event at most
+// min(its tracks, capacity) (seeds without tracks are written directly).
+inline long long work_capacity(long long n_tracks, long long n_events, int cap) {
+  long long c = cap < pvdev::kMaxSeeds ? cap : pvdev::kMaxSeeds;
+  long long by_events = n_events * c;
+  return by_events < n_tracks ? by_events : n_tracks;
+}
 
 int fused_blocks_per_sm(int nbins, int mode);
 int fit_blocks_per_sm(bool kahan);
