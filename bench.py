@@ -329,8 +329,9 @@ def run_ours(args):
                    f"({N_REPLICAS * batch.n_tracks * 44 / 1e6:.0f} MB > 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes},
+                     "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                     "kernel": "fused step: find_kernel<3> + fit_kernel<0> (one launch each)"},
         "plain": {"value": E * world / (plain_ms / 1e3), "ms_per_step": plain_ms,
                   "path": "one kernel per step, global-memory histograms"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
