@@ -156,8 +156,8 @@ struct SeedOut {   // shared-memory seed table of one event
 // running maximum of the open piece (L) and the next maximum (R) if both the
 // piece [s, m] and the rest [m+1, b] hold the minimal integral.
 template <class Emit>
-__device__ void split_walk(const uint32_t* N, int a, int b, uint64_t total, const Consts& C,
-                           Emit&& emit) {
+__host__ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t total,
+                                    const Consts& C, Emit&& emit) {
   int s = a;
   uint64_t pre_s = 0;                 // sum over [a, s)
   int top = a;
@@ -197,7 +197,7 @@ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t total, cons
   emit(s, b, total - pre_s);
 }
 
-__device__ __forceinline__ int argmax_bins(const uint32_t* N, int lo, int hi) {
+__host__ __device__ __forceinline__ int argmax_bins(const uint32_t* N, int lo, int hi) {
   int best = lo;
   uint32_t bv = N[lo];
   for (int i = lo + 1; i <= hi; ++i)
@@ -205,8 +205,8 @@ __device__ __forceinline__ int argmax_bins(const uint32_t* N, int lo, int hi) {
   return best;
 }
 
-__device__ __forceinline__ bool keep_piece(const uint32_t* N, int lo, int hi, uint64_t integral,
-                                           const Consts& C, int* im) {
+__host__ __device__ __forceinline__ bool keep_piece(const uint32_t* N, int lo, int hi,
+                                                    uint64_t integral, const Consts& C, int* im) {
   *im = argmax_bins(N, lo, hi);
   uint64_t T = (*im < C.gas_bin) ? C.t_gas : C.t_pp;
   return integral >= T;

@@ -1,0 +1,102 @@
+"""The library's peak-search walk (split_walk, compiled for the host) finds
+the same seed clusters and maximum bins as the oracle (Sec. 3.3, reading R5)
+on hand-built and random histograms.  CPU only."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+P = oracle.default_params()
+NB = oracle.num_bins(P)
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    from paper_2412_14966_gb300 import build
+    out = str(tmp_path_factory.mktemp("walk") / "walk_harness.so")
+    subprocess.run([build._nvcc(), *build.ARCH, "-O2", "-std=c++17", "-shared", "-Xcompiler",
+                    "-fPIC", "--expt-relaxed-constexpr", "-I", build.INCLUDE, "-I", build.CSRC,
+                    os.path.join(ROOT, "tests", "walk_harness.cu"), "-o", out], check=True)
+    lib = C.CDLL(out)
+    ip = C.POINTER(C.c_int32)
+    lib.harness_seeds.argtypes = [C.POINTER(C.c_uint32), C.c_int, C.c_uint32, C.c_uint32,
+                                  C.c_uint32, C.c_int, C.c_int, C.c_int, ip, ip, ip, C.c_int]
+    lib.harness_seeds.restype = C.c_int
+    return lib
+
+
+def _gpu_walk(lib, N):
+    N = np.ascontiguousarray(N, np.uint32)
+    cap = 4096
+    lo = np.zeros(cap, np.int32); hi = np.zeros(cap, np.int32); bn = np.zeros(cap, np.int32)
+    t_pp = int(round(P.min_integral_pp * oracle.ONE))
+    t_gas = int(round(P.min_integral_gas * oracle.ONE))
+    ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    n = lib.harness_seeds(N.ctypes.data_as(C.POINTER(C.c_uint32)), NB, P.bin_threshold, t_pp,
+                          t_gas, P.dip_num, P.dip_den, oracle.gas_bin(P), ip(lo), ip(hi), ip(bn),
+                          cap)
+    return list(zip(lo[:n].tolist(), hi[:n].tolist(), bn[:n].tolist()))
+
+
+def _oracle(N):
+    s = oracle.seeds_from_hist(np.ascontiguousarray(N, np.uint32), P)
+    return list(zip(s["lo"].tolist(), s["hi"].tolist(), s["bin"].tolist()))
+
+
+def _hist(start, vals):
+    h = np.zeros(NB, np.uint32)
+    h[start:start + len(vals)] = vals
+    return h
+
+
+HAND = [
+    (2000, [1000, 3000, 5000, 3000, 1000]),
+    (2000, [1000, 4000, 8000, 4000, 1500, 4000, 8000, 4000, 1000]),
+    (2000, [1000, 4000, 8000, 7000, 6400, 7000, 8000, 4000, 1000]),
+    (2000, [1000, 4000, 8000, 7000, 6399, 7000, 8000, 4000, 1000]),
+    (2000, [2000, 6000, 12000, 6000, 1000, 1500, 2500, 1500, 500]),
+    (2500, [1000, 3000, 2192, 1000, 1000]),
+    (500, [1000, 3000, 2192, 1000, 1000]),
+    (2000, [4000, 12000, 2000, 12000, 4000]),
+    (2000, [3000, 12000, 3000, 1000, 1000, 1000, 3000, 12000, 3000]),
+    (2000, [3000, 12000, 3000, 300, 3000, 4000, 300, 3000, 12000, 3000]),
+    (2000, [2000, 5000, 2240, 1000, 4000, 9000, 4000]),
+    (2000, [3000, 6000, 3000, 1000, 8000, 20000, 12000, 20000, 8000, 3000]),
+    (2000, [9000, 9000, 9000, 100, 9000, 9000]),
+    (0, [9000, 12000, 300, 12000, 9000]),
+    (NB - 5, [9000, 12000, 300, 12000, 9000]),
+    (995, [3000, 9000, 3000, 500, 3000, 9000, 3000]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(HAND)))
+def test_walk_hand_built(harness, case):
+    start, vals = HAND[case]
+    h = _hist(start, vals)
+    assert _gpu_walk(harness, h) == _oracle(h)
+
+
+def test_walk_random_histograms(harness):
+    rng = np.random.default_rng(31)
+    for trial in range(2000):
+        N = np.zeros(NB, np.int64)
+        for _ in range(rng.integers(1, 10)):
+            c = rng.integers(20, NB - 20)
+            w = rng.integers(1, 6)
+            amp = rng.integers(300, 25000)
+            for j in range(c - 3 * w, c + 3 * w + 1):
+                N[j] += int(amp * np.exp(-0.5 * ((j - c) / w) ** 2))
+        noise = rng.integers(-400, 400, NB)
+        N = np.maximum(N + np.where(N > 0, noise, 0), 0)
+        for _ in range(rng.integers(0, 3)):          # plateaus
+            k = rng.integers(0, NB - 6)
+            N[k:k + rng.integers(2, 5)] = N[k]
+        if trial % 7 == 0:                           # a gas-region cluster
+            N[990:1010] = rng.integers(100, 6000, 20)
+        N = N.astype(np.uint32)
+        assert _gpu_walk(harness, N) == _oracle(N), trial
