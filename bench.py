@@ -191,6 +191,81 @@ def cpu_baseline(batch, max_seconds: float = 15.0) -> dict:
             "sample": f"first {n} of {batch.n_events} events of the workload, one thread"}
 
 
+def serving_run(pv, ctx, offered_hz: float, duration_s: float = 1.0, tick_s: float = 100e-6,
+                seed: int = 7) -> dict:
+    """Open-loop serving: events of the uneven mixture workload (mu ~ U(1, 12),
+    20% fixed-target) arrive as a Poisson process at offered_hz; the events of
+    each tick form one request, submitted with pv_submit and polled with
+    pv_poll.  Latency of a request = completion - arrival (host lag included)."""
+    import torch
+    from paper_2412_14966_gb300 import synthetic
+    rng = np.random.default_rng(seed)
+    mix = synthetic.workload_mixture(n_events=20000, seed=seed)
+    n_ticks = int(duration_s / tick_s)
+    counts = rng.poisson(offered_hz * tick_s, size=n_ticks)
+    # a ring of device request buffers, reused once their request is done
+    n_slots = 128
+    slots = []
+    start = 0
+    for i in range(n_slots):
+        k = int(max(1, counts[i % n_ticks]))
+        ev = np.arange(start, start + k) % mix.n_events
+        start += k
+        b = mix.subset(ev)
+        slots.append({"batch": b, "tracks": pv.Tracks.from_batch(b),
+                      "out": pv.Vertices.empty(b.n_events, b.n_tracks), "ticket": None,
+                      "arrival": 0.0, "submit": 0.0})
+    torch.cuda.synchronize()
+    lat = []
+    served = 0
+    t0 = time.perf_counter()
+    first = None
+
+    def retire(sl):
+        nonlocal served
+        ns = ctx.latency_ns(sl["ticket"])
+        lat.append((sl["submit"] - sl["arrival"]) + ns * 1e-9)
+        served += sl["batch"].n_events
+        sl["ticket"] = None
+
+    for i in range(n_ticks):
+        arrival = t0 + (i + 1) * tick_s
+        while time.perf_counter() < arrival:
+            pass
+        sl = slots[i % n_slots]
+        while sl["ticket"] is not None:           # slot still in flight: back-pressure
+            if ctx.poll(sl["ticket"]):
+                retire(sl)
+        sl["arrival"] = arrival
+        sl["submit"] = time.perf_counter()
+        while True:
+            rc, tk = ctx.submit_nowait(sl["tracks"], sl["out"])
+            if rc == pv.PV_OK:
+                break
+            for other in slots:
+                if other["ticket"] is not None and ctx.poll(other["ticket"]):
+                    retire(other)
+        sl["ticket"] = tk
+        if first is None:
+            first = arrival
+        # opportunistic polling of the oldest requests
+        for j in range(1, 4):
+            o = slots[(i - n_slots + j) % n_slots]
+            if o["ticket"] is not None and ctx.poll(o["ticket"]):
+                retire(o)
+    for sl in slots:
+        while sl["ticket"] is not None:
+            if ctx.poll(sl["ticket"]):
+                retire(sl)
+    t_end = time.perf_counter()
+    lat_ms = np.array(lat) * 1e3
+    return {"offered_events_per_s": offered_hz, "events_per_s": served / (t_end - first),
+            "requests": len(lat), "tick_us": tick_s * 1e6,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "p999_ms": float(np.percentile(lat_ms, 99.9)),
+            "workload": "mixture: mu ~ U(1,12) per event, 20% fixed-target; Poisson arrivals"}
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle timed as the reference arm."""
     world, rank, local = _dist_env()
@@ -339,6 +414,8 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": launches,
     }
+    if args.serve_rate > 0:
+        line["serving"] = serving_run(pv, ctx, args.serve_rate)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch)
     ctx.close()
@@ -355,6 +432,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--serve-rate", type=float, default=10e6,
+                    help="offered events/s of the serving leg (0 = skip it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
