@@ -86,6 +86,9 @@ typedef struct {
   float max_r_beam;                 /* final transverse cut for pp vertices (Sec. 3.5): 0.3 mm */
   int32_t accum_mode;               /* PV_ACCUM_*: default PV_ACCUM_FP32 */
   int32_t path;                     /* PV_PATH_*: default PV_PATH_FUSED */
+  int32_t use_graph;                /* 1: the fused find+fit launch is captured once per
+                                       argument set as a CUDA graph and replayed: default 0 */
+  int32_t reserved;                 /* 0 */
   uint64_t pool_bytes;              /* serving: device bytes admitted requests may pin (0 = 1 GiB) */
   uint64_t max_spin_ns;             /* serving: bound of every wait (0 = 10 s) */
 } pv_config;
@@ -211,6 +214,26 @@ int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns);
  * device memory as for pv_fit_batch; the context's path setting is ignored
  * (always the fused kernel).  Asynchronous on cuda_stream. */
 int pv_find_fit_static(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, void* cuda_stream);
+
+/* Project-written autotuner of the fused path's launch shape.  Runs the fused
+ * find+fit on `sample` (device tracks) into `out` (device) with every
+ * candidate pair of block sizes (find kernel 64/128/256 threads, fit kernel
+ * 128/256), each with its occupancy-sized persistent grid, times them with
+ * CUDA events on cuda_stream, and keeps the fastest for the sample's
+ * event-size bucket (mean tracks per event below 300, below 800, 800 and
+ * more).  Later launches on batches of that bucket use it.  The results of
+ * the method do not depend on the launch shape.  Synchronises cuda_stream. */
+int pv_autotune(pv_ctx* ctx, const pv_tracks* sample, pv_vertices* out, void* cuda_stream);
+
+/* The launch shape the fused path would use for `tracks`: block sizes of the
+ * find and fit kernels (any pointer may be NULL). */
+int pv_launch_config(const pv_ctx* ctx, const pv_tracks* tracks, int* find_threads,
+                     int* fit_threads, int* find_grid, int* fit_grid);
+
+/* Set the launch shape of an event-size bucket (0: mean tracks per event
+ * below 300, 1: below 800, 2: 800 and more) by hand: find kernel 64, 128 or
+ * 256 threads, fit kernel 128 or 256.  PV_ERR_ARG for other values. */
+int pv_set_launch_config(pv_ctx* ctx, int bucket, int find_threads, int fit_threads);
 
 /* Human-readable name of an error code. */
 const char* pv_strerror(int code);

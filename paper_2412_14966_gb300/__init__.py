@@ -32,7 +32,7 @@ EXPORTED = (
     "pv_config_default", "pv_init", "pv_destroy", "pv_find_batch", "pv_fit_batch",
     "pv_extrapolate_batch", "pv_histogram_batch", "pv_num_bins", "pv_run_host", "pv_submit",
     "pv_poll", "pv_request_latency_ns", "pv_strerror", "pv_last_cuda_error", "pv_launch_count",
-    "pv_find_fit_static",
+    "pv_find_fit_static", "pv_autotune", "pv_launch_config", "pv_set_launch_config",
 )
 
 
@@ -60,6 +60,7 @@ class pv_config(C.Structure):
         ("chi2_max", C.c_float), ("dchi2_tol", C.c_float), ("dz_tol", C.c_float),
         ("max_iter", C.c_int32), ("max_r_beam", C.c_float),
         ("accum_mode", C.c_int32), ("path", C.c_int32),
+        ("use_graph", C.c_int32), ("reserved", C.c_int32),
         ("pool_bytes", C.c_uint64), ("max_spin_ns", C.c_uint64),
     ]
 
@@ -120,6 +121,10 @@ def load():
     L.pv_launch_count.argtypes = [C.c_void_p]
     L.pv_launch_count.restype = C.c_uint64
     L.pv_find_fit_static.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
+    L.pv_autotune.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
+    L.pv_set_launch_config.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.pv_launch_config.argtypes = [C.c_void_p, P(pv_tracks), P(C.c_int), P(C.c_int), P(C.c_int),
+                                   P(C.c_int)]
     _LIB = L
     return L
 
@@ -325,6 +330,27 @@ class Context:
         self._check(self.lib.pv_find_fit_static(self.h, C.byref(t), C.byref(o),
                                                 _stream_handle(stream)), "pv_find_fit_static")
         return out
+
+    def autotune(self, tracks: Tracks, out: Vertices | None = None, stream=None) -> tuple:
+        """``pv_autotune`` on a sample batch; returns the chosen launch shape."""
+        out = out or Vertices.empty(tracks.n_events, tracks.n_tracks)
+        t, o = tracks.struct(), out.struct()
+        self._check(self.lib.pv_autotune(self.h, C.byref(t), C.byref(o), _stream_handle(stream)),
+                    "pv_autotune")
+        return self.launch_config(tracks)
+
+    def set_launch_config(self, bucket: int, find_threads: int, fit_threads: int):
+        """``pv_set_launch_config``: block sizes of one event-size bucket."""
+        self._check(self.lib.pv_set_launch_config(self.h, bucket, find_threads, fit_threads),
+                    "pv_set_launch_config")
+
+    def launch_config(self, tracks: Tracks) -> tuple:
+        """(find threads, fit threads, find grid, fit grid) the fused path would use."""
+        t = tracks.struct()
+        v = [C.c_int() for _ in range(4)]
+        self._check(self.lib.pv_launch_config(self.h, C.byref(t), *[C.byref(x) for x in v]),
+                    "pv_launch_config")
+        return tuple(x.value for x in v)
 
     # -- host entry point -----------------------------------------------------
     def run_host(self, tracks: Tracks, out: Vertices, stream=None) -> Vertices:

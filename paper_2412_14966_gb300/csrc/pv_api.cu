@@ -202,8 +202,14 @@ struct pv_ctx {
   pv_beamline beam{};
   Consts C{};
   int n_sm = 0;
-  int fused_grid[4] = {0, 0, 0, 0};   // find kernel, by mode
-  int fit_grid[2] = {0, 0};           // fit kernel: binary32, compensated
+  // launch shapes: per event-size bucket, chosen by pv_autotune (default:
+  // 128-thread find CTAs, 256-thread fit CTAs, occupancy-sized grids)
+  pvk::LaunchCfg bucket_cfg[3];
+  int find_per_sm[4][3] = {};         // [mode][64/128/256]
+  int fit_per_sm[2][2] = {};          // [kahan][128/256]
+  // CUDA graphs of the fused launch, keyed by its arguments
+  std::map<std::string, cudaGraphExec_t> graphs;
+  cudaStream_t capture_stream = nullptr;
   DevBuf fused_ws, plain_ws;
   // host-buffer entry point staging
   DevBuf host_in, host_out;
@@ -344,18 +350,87 @@ pvk::SeedPtrs seed_ptrs(const pv_vertices* s) {
   return S;
 }
 
+int nt_index(int nt) { return nt == 64 ? 0 : (nt == 256 ? 2 : 1); }
+
+int bucket_of(const pv_tracks* t) {
+  double mean = t->n_events > 0 ? static_cast<double>(t->n_tracks) / t->n_events : 0.0;
+  return mean < 300.0 ? 0 : (mean < 800.0 ? 1 : 2);
+}
+
+// Block sizes from the bucket's configuration, grids from occupancy, capped by
+// the work there is.
+pvk::LaunchCfg launch_cfg(const pv_ctx* ctx, int mode, const pv_tracks* t, int find_nt,
+                          int fit_nt) {
+  pvk::LaunchCfg L;
+  L.find_nt = find_nt;
+  L.fit_nt = fit_nt;
+  int per = ctx->find_per_sm[mode][nt_index(find_nt)];
+  long long g = static_cast<long long>(ctx->n_sm) * (per > 0 ? per : 1);
+  if (g > t->n_events) g = t->n_events > 0 ? t->n_events : 1;
+  L.find_grid = static_cast<int>(g);
+  int fper = ctx->fit_per_sm[ctx->C.accum_mode == PV_ACCUM_KAHAN ? 1 : 0][fit_nt == 128 ? 0 : 1];
+  L.fit_grid = ctx->n_sm * (fper > 0 ? fper : 1);
+  return L;
+}
+
+pvk::LaunchCfg chosen_cfg(const pv_ctx* ctx, int mode, const pv_tracks* t) {
+  const pvk::LaunchCfg& b = ctx->bucket_cfg[bucket_of(t)];
+  return launch_cfg(ctx, mode, t, b.find_nt, b.fit_nt);
+}
+
 // Enqueue the fused kernels with scratch at `base` (laid out by FusedLayout).
-int enqueue_fused(pv_ctx* ctx, int mode, const pv_tracks* tracks, const pv_vertices* seeds,
-                  const pv_vertices* out, void* base, cudaStream_t st) {
+int enqueue_fused_cfg(pv_ctx* ctx, int mode, const pv_tracks* tracks, const pv_vertices* seeds,
+                      const pv_vertices* out, void* base, const pvk::LaunchCfg& cfg,
+                      cudaStream_t st) {
   FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
-  int grid = ctx->fused_grid[mode];
-  if (grid < 1) grid = ctx->n_sm;
-  int fit_grid = ctx->fit_grid[ctx->C.accum_mode == PV_ACCUM_KAHAN ? 1 : 0];
-  if (fit_grid < 1) fit_grid = ctx->n_sm;
   int n = 0;
   PV_CUDA(ctx, pvk::launch_fused(mode, ctx->C, track_ptrs(tracks), seed_ptrs(seeds),
-                                 out_ptrs(out), L.scratch(base), grid, fit_grid, st, &n));
+                                 out_ptrs(out), L.scratch(base), cfg, st, &n));
   ctx->launches += n;
+  return PV_OK;
+}
+
+int enqueue_fused(pv_ctx* ctx, int mode, const pv_tracks* tracks, const pv_vertices* seeds,
+                  const pv_vertices* out, void* base, cudaStream_t st) {
+  return enqueue_fused_cfg(ctx, mode, tracks, seeds, out, base, chosen_cfg(ctx, mode, tracks), st);
+}
+
+void clear_graphs(pv_ctx* ctx) {
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+}
+
+// The fused find+fit as a replayed CUDA graph (one per argument set).
+int enqueue_fused_graph(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* out, void* base,
+                        cudaStream_t st) {
+  const pvk::LaunchCfg cfg = chosen_cfg(ctx, pvk::kFindFit, tracks);
+  std::string key;
+  key.append(reinterpret_cast<const char*>(tracks), sizeof(pv_tracks));
+  key.append(reinterpret_cast<const char*>(out), sizeof(pv_vertices));
+  key.append(reinterpret_cast<const char*>(&cfg), sizeof(cfg));
+  key.append(reinterpret_cast<const char*>(&base), sizeof(base));
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    if (ctx->graphs.size() >= 64) clear_graphs(ctx);
+    if (!ctx->capture_stream)
+      PV_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    PV_CUDA(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
+    int n = 0;
+    cudaError_t err = pvk::launch_fused(pvk::kFindFit, ctx->C, track_ptrs(tracks), seed_ptrs(nullptr),
+                                        out_ptrs(out), L.scratch(base), cfg, ctx->capture_stream, &n);
+    cudaGraph_t graph = nullptr;
+    cudaError_t err2 = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return fail_cuda(ctx, err); }
+    if (err2 != cudaSuccess) return fail_cuda(ctx, err2);
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return fail_cuda(ctx, err);
+    it = ctx->graphs.emplace(key, exec).first;
+  }
+  PV_CUDA(ctx, cudaGraphLaunch(it->second, st));
+  ctx->launches += 2;
   return PV_OK;
 }
 
@@ -379,7 +454,11 @@ int run_find_or_fit(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* see
     return PV_OK;
   }
   FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
+  void* before = ctx->fused_ws.p;
   PV_CUDA(ctx, ctx->fused_ws.ensure(L.total));
+  if (ctx->fused_ws.p != before) clear_graphs(ctx);   // graphs hold the old scratch
+  if (ctx->cfg.use_graph && mode == pvk::kFindFit)
+    return enqueue_fused_graph(ctx, tracks, out, ctx->fused_ws.p, st);
   return enqueue_fused(ctx, mode, tracks, seeds, out, ctx->fused_ws.p, st);
 }
 
@@ -472,6 +551,8 @@ void pv_config_default(pv_config* c) {
   c->max_r_beam = 0.3f;
   c->accum_mode = PV_ACCUM_FP32;
   c->path = PV_PATH_FUSED;
+  c->use_graph = 0;
+  c->reserved = 0;
   c->pool_bytes = 0;
   c->max_spin_ns = 0;
 }
@@ -500,14 +581,12 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
     delete ctx;
     return PV_ERR_CUDA;
   }
-  for (int mode = 1; mode <= 3; ++mode) {
-    int per_sm = pvk::fused_blocks_per_sm(C.nbins, mode);
-    ctx->fused_grid[mode] = ctx->n_sm * (per_sm > 0 ? per_sm : 1);
-  }
-  for (int k = 0; k < 2; ++k) {
-    int per_sm = pvk::fit_blocks_per_sm(k == 1);
-    ctx->fit_grid[k] = ctx->n_sm * (per_sm > 0 ? per_sm : 1);
-  }
+  const int nts[3] = {64, 128, 256};
+  for (int mode = 1; mode <= 3; ++mode)
+    for (int i = 0; i < 3; ++i) ctx->find_per_sm[mode][i] = pvk::fused_blocks_per_sm(C.nbins, mode, nts[i]);
+  for (int k = 0; k < 2; ++k)
+    for (int i = 0; i < 2; ++i) ctx->fit_per_sm[k][i] = pvk::fit_blocks_per_sm(k == 1, i == 0 ? 128 : 256);
+  for (int b = 0; b < 3; ++b) ctx->bucket_cfg[b] = pvk::LaunchCfg{128, 0, pvk::kFitThreads, 0};
   *out = ctx;
   return PV_OK;
 }
@@ -538,6 +617,8 @@ int pv_destroy(pv_ctx* ctx) {
   }
   if (rc != PV_OK) return rc;   // leave the context alive: its requests still run
   cudaDeviceSynchronize();
+  clear_graphs(ctx);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   ctx->fused_ws.release();
   ctx->plain_ws.release();
   ctx->host_in.release();
@@ -830,4 +911,70 @@ extern "C" int pv_find_fit_static(pv_ctx* ctx, const pv_tracks* tracks, pv_verti
   // enqueue_fused clears the work counters on the stream before the kernels
   return enqueue_fused(ctx, pvk::kFindFit, tracks, nullptr, out, base,
                        static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pv_launch_config(const pv_ctx* ctx, const pv_tracks* tracks, int* find_threads,
+                                int* fit_threads, int* find_grid, int* fit_grid) {
+  if (!ctx || !tracks) return PV_ERR_ARG;
+  const pvk::LaunchCfg L = chosen_cfg(ctx, pvk::kFindFit, tracks);
+  if (find_threads) *find_threads = L.find_nt;
+  if (fit_threads) *fit_threads = L.fit_nt;
+  if (find_grid) *find_grid = L.find_grid;
+  if (fit_grid) *fit_grid = L.fit_grid;
+  return PV_OK;
+}
+
+extern "C" int pv_autotune(pv_ctx* ctx, const pv_tracks* sample, pv_vertices* out, void* stream) {
+  if (!ctx) return PV_ERR_ARG;
+  int rc = check_tracks(sample);
+  if (rc != PV_OK) return rc;
+  rc = check_out(out, sample, true);
+  if (rc != PV_OK) return rc;
+  if (sample->n_events == 0) return PV_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FusedLayout FL(sample->n_tracks, sample->n_events, out->capacity);
+  void* before = ctx->fused_ws.p;
+  PV_CUDA(ctx, ctx->fused_ws.ensure(FL.total));
+  if (ctx->fused_ws.p != before) clear_graphs(ctx);
+  cudaEvent_t e0, e1;
+  PV_CUDA(ctx, cudaEventCreate(&e0));
+  PV_CUDA(ctx, cudaEventCreate(&e1));
+  const int finds[3] = {64, 128, 256};
+  const int fits[2] = {128, 256};
+  float best = -1.f;
+  pvk::LaunchCfg best_cfg{128, 0, pvk::kFitThreads, 0};
+  for (int fi : finds) {
+    for (int ft : fits) {
+      const pvk::LaunchCfg cfg = launch_cfg(ctx, pvk::kFindFit, sample, fi, ft);
+      float t_min = -1.f;
+      for (int rep = 0; rep < 4; ++rep) {
+        PV_CUDA(ctx, cudaEventRecord(e0, st));
+        rc = enqueue_fused_cfg(ctx, pvk::kFindFit, sample, nullptr, out, ctx->fused_ws.p, cfg, st);
+        if (rc != PV_OK) return rc;
+        PV_CUDA(ctx, cudaEventRecord(e1, st));
+        PV_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PV_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0 && (t_min < 0.f || ms < t_min)) t_min = ms;   // the first run warms up
+      }
+      if (best < 0.f || t_min < best) {
+        best = t_min;
+        best_cfg = pvk::LaunchCfg{fi, 0, ft, 0};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->bucket_cfg[bucket_of(sample)] = best_cfg;
+  clear_graphs(ctx);
+  return PV_OK;
+}
+
+extern "C" int pv_set_launch_config(pv_ctx* ctx, int bucket, int find_threads, int fit_threads) {
+  if (!ctx || bucket < 0 || bucket > 2) return PV_ERR_ARG;
+  if (!pvk::find_block_ok(find_threads) || !pvk::fit_block_ok(fit_threads)) return PV_ERR_ARG;
+  ctx->bucket_cfg[bucket] = pvk::LaunchCfg{find_threads, 0, fit_threads, 0};
+  clear_graphs(ctx);
+  return PV_OK;
 }

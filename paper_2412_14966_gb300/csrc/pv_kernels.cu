@@ -181,8 +181,8 @@ __device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tr
 //           position is left in the output row, which the fit overwrites.
 // kFit:     seeds and assignments from the caller, then fit inputs and work.
 
-template <int MODE>
-__global__ void __launch_bounds__(kFusedThreads)
+template <int MODE, int NT>
+__global__ void __launch_bounds__(NT)
 find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Layout Lo = make_layout(C.nbins, MODE);
@@ -204,7 +204,6 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  constexpr int NT = kFusedThreads;
   constexpr int NW = NT / 32;
 
   if (MODE & kFind) {
@@ -372,8 +371,8 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
 // vertex fit kernel (fused path, stage 2): every 8-lane group fits one vertex
 // of any event; warps take 4 work items at a time.
 
-template <bool kKahan>
-__global__ void __launch_bounds__(kFitThreads)
+template <bool kKahan, int FT>
+__global__ void __launch_bounds__(FT)
 fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
   const int lane = threadIdx.x & 31;
   const int r = lane & (kGroup - 1);
@@ -415,65 +414,108 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
   }
 }
 
-template <int MODE>
+// ---------------------------------------------------------------------------
+// launch plumbing: kernel instantiations by block size
+
+template <int MODE, int NT>
 static cudaError_t setup_find(int nbins) {
-  cudaError_t err = cudaFuncSetAttribute(find_kernel<MODE>,
+  cudaError_t err = cudaFuncSetAttribute(find_kernel<MODE, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)fused_smem_bytes(nbins, MODE));
   if (err != cudaSuccess) return err;
-  return cudaFuncSetAttribute(find_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  return cudaFuncSetAttribute(find_kernel<MODE, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
+}
+
+template <int NT>
+static cudaError_t setup_find_all(int nbins) {
+  cudaError_t err;
+  if ((err = setup_find<kFind, NT>(nbins)) != cudaSuccess) return err;
+  if ((err = setup_find<kFit, NT>(nbins)) != cudaSuccess) return err;
+  return setup_find<kFindFit, NT>(nbins);
 }
 
 cudaError_t fused_setup(int nbins) {
   cudaError_t err;
-  if ((err = setup_find<kFind>(nbins)) != cudaSuccess) return err;
-  if ((err = setup_find<kFit>(nbins)) != cudaSuccess) return err;
-  return setup_find<kFindFit>(nbins);
+  if ((err = setup_find_all<64>(nbins)) != cudaSuccess) return err;
+  if ((err = setup_find_all<128>(nbins)) != cudaSuccess) return err;
+  return setup_find_all<256>(nbins);
 }
 
-template <int MODE>
+bool find_block_ok(int nt) { return nt == 64 || nt == 128 || nt == 256; }
+bool fit_block_ok(int ft) { return ft == 128 || ft == 256; }
+
+template <int MODE, int NT>
 static int find_blocks(int nbins) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, find_kernel<MODE>, kFusedThreads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, find_kernel<MODE, NT>, NT,
                                                     fused_smem_bytes(nbins, MODE)) != cudaSuccess)
     return 0;
   return blocks;
 }
 
-int fused_blocks_per_sm(int nbins, int mode) {
-  if (mode == kFind) return find_blocks<kFind>(nbins);
-  if (mode == kFit) return find_blocks<kFit>(nbins);
-  return find_blocks<kFindFit>(nbins);
+template <int NT>
+static int find_blocks_nt(int nbins, int mode) {
+  if (mode == kFind) return find_blocks<kFind, NT>(nbins);
+  if (mode == kFit) return find_blocks<kFit, NT>(nbins);
+  return find_blocks<kFindFit, NT>(nbins);
 }
 
-int fit_blocks_per_sm(bool kahan) {
+int fused_blocks_per_sm(int nbins, int mode, int nt) {
+  if (nt == 64) return find_blocks_nt<64>(nbins, mode);
+  if (nt == 256) return find_blocks_nt<256>(nbins, mode);
+  return find_blocks_nt<128>(nbins, mode);
+}
+
+template <bool K, int FT>
+static int fit_blocks(void) {
   int blocks = 0;
-  cudaError_t err = kahan ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fit_kernel<true>,
-                                                                          kFitThreads, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fit_kernel<false>,
-                                                                          kFitThreads, 0);
-  return err == cudaSuccess ? blocks : 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fit_kernel<K, FT>, FT, 0) !=
+      cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+int fit_blocks_per_sm(bool kahan, int ft) {
+  if (ft == 128) return kahan ? fit_blocks<true, 128>() : fit_blocks<false, 128>();
+  return kahan ? fit_blocks<true, 256>() : fit_blocks<false, 256>();
+}
+
+template <int MODE, int NT>
+static void launch_find_nt(int grid, size_t sm, cudaStream_t st, const Consts& C,
+                           const TrackPtrs& T, const SeedPtrs& S, const OutPtrs& O,
+                           const TrackScratch& ws) {
+  find_kernel<MODE, NT><<<grid, NT, sm, st>>>(C, T, S, O, ws);
+}
+
+template <int MODE>
+static void launch_find(int nt, int grid, size_t sm, cudaStream_t st, const Consts& C,
+                        const TrackPtrs& T, const SeedPtrs& S, const OutPtrs& O,
+                        const TrackScratch& ws) {
+  if (nt == 64) launch_find_nt<MODE, 64>(grid, sm, st, C, T, S, O, ws);
+  else if (nt == 256) launch_find_nt<MODE, 256>(grid, sm, st, C, T, S, O, ws);
+  else launch_find_nt<MODE, 128>(grid, sm, st, C, T, S, O, ws);
 }
 
 cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
-                         const OutPtrs& O, const TrackScratch& ws, int find_grid, int fit_grid,
+                         const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
                          cudaStream_t st, int* n_launches) {
   size_t sm = fused_smem_bytes(C.nbins, mode);
   cudaError_t err = cudaMemsetAsync(ws.counters, 0, 4 * sizeof(int), st);
   if (err != cudaSuccess) return err;
-  if (mode == kFind)
-    find_kernel<kFind><<<find_grid, kFusedThreads, sm, st>>>(C, T, S, O, ws);
-  else if (mode == kFit)
-    find_kernel<kFit><<<find_grid, kFusedThreads, sm, st>>>(C, T, S, O, ws);
-  else
-    find_kernel<kFindFit><<<find_grid, kFusedThreads, sm, st>>>(C, T, S, O, ws);
+  if (mode == kFind) launch_find<kFind>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
+  else if (mode == kFit) launch_find<kFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
+  else launch_find<kFindFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
   ++*n_launches;
   if (mode & kFit) {
-    if (C.accum_mode == PV_ACCUM_KAHAN)
-      fit_kernel<true><<<fit_grid, kFitThreads, 0, st>>>(C, T, ws, O);
-    else
-      fit_kernel<false><<<fit_grid, kFitThreads, 0, st>>>(C, T, ws, O);
+    const bool kahan = C.accum_mode == PV_ACCUM_KAHAN;
+    if (L.fit_nt == 128) {
+      if (kahan) fit_kernel<true, 128><<<L.fit_grid, 128, 0, st>>>(C, T, ws, O);
+      else fit_kernel<false, 128><<<L.fit_grid, 128, 0, st>>>(C, T, ws, O);
+    } else {
+      if (kahan) fit_kernel<true, 256><<<L.fit_grid, 256, 0, st>>>(C, T, ws, O);
+      else fit_kernel<false, 256><<<L.fit_grid, 256, 0, st>>>(C, T, ws, O);
+    }
     ++*n_launches;
   }
   return cudaGetLastError();

@@ -86,11 +86,24 @@ struct PlainScratch {
 size_t fused_smem_bytes(int nbins, int mode);
 cudaError_t fused_setup(int nbins);
 
+// Launch shape of the fused path (block sizes and persistent grids); results do
+// not depend on it.
+struct LaunchCfg {
+  int find_nt, find_grid;
+  int fit_nt, fit_grid;
+};
+
 // Enqueues the fused path: counter reset, find kernel, then (modes with a fit)
 // the vertex fit kernel.  *n_launches receives the kernels enqueued.
 cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, const SeedPtrs& S,
-                         const OutPtrs& O, const TrackScratch& ws, int find_grid, int fit_grid,
+                         const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
                          cudaStream_t st, int* n_launches);
+
+bool find_block_ok(int nt);
+bool fit_block_ok(int ft);
+int fused_blocks_per_sm(int nbins, int mode, int nt);
+int fit_blocks_per_sm(bool kahan, int ft);
+constexpr int kFitThreads = 256;
 
 // Upper bound of the vertices a batch can list: per event at most
 // min(its tracks, capacity) (seeds without tracks are written directly).
@@ -102,7 +115,6 @@ inline long long work_capacity(long long n_tracks, long long n_events, int cap) 
 
 int fused_blocks_per_sm(int nbins, int mode);
 int fit_blocks_per_sm(bool kahan);
-constexpr int kFitThreads = 256;
 
 cudaError_t launch_plain_find(const pvdev::Consts& C, const TrackPtrs& T, const OutPtrs& O,
                               const PlainScratch& ws, cudaStream_t st, int* n_launches);
