@@ -141,11 +141,10 @@ def _dist_env():
     return world, rank, local
 
 
-def _init_dist(world):
+def _init_dist(world, backend: str = "nccl"):
     if world <= 1:
         return None
     import torch.distributed as dist
-    backend = "nccl"
     dist.init_process_group(backend=backend)
     return dist
 
@@ -155,22 +154,39 @@ def _barrier(dist):
         dist.barrier()
 
 
-def _max_over_ranks(dist, value: float) -> float:
+def _reduce(dist, value: float, op: str) -> float:
+    """All-reduce of one host scalar over the ranks (NCCL: through the device)."""
     if dist is None:
         return value
     import torch
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def _max_over_ranks(dist, value: float) -> float:
+    return _reduce(dist, value, "max")
 
 
 def _sum_over_ranks(dist, value: float) -> float:
-    if dist is None:
-        return value
-    import torch
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(dist, value, "sum")
+
+
+def shard_workload(rank: int, n_events: int | None = None):
+    """Rank r's shard: its own independent events (weak scaling, no exchange);
+    the generator seed is 1 + r, so rank 0 runs the single-GPU workload."""
+    from paper_2412_14966_gb300 import synthetic
+    if n_events is None:
+        return synthetic.workload_nominal(seed=1 + rank)
+    return synthetic.workload_nominal(n_events=n_events, seed=1 + rank)
+
+
+def aggregate(dist, events_local: float, seconds_local: float):
+    """Whole-job throughput: events of all ranks over the slowest rank's time."""
+    total_s = _max_over_ranks(dist, seconds_local)
+    events_all = _sum_over_ranks(dist, events_local)
+    return events_all, total_s, events_all / total_s
 
 
 def cpu_baseline(batch, max_seconds: float = 15.0) -> dict:
@@ -318,7 +334,7 @@ def run_ours(args):
     dist = _init_dist(world)
     build.build()
 
-    batch = synthetic.workload_nominal(seed=1 + rank)
+    batch = shard_workload(rank)
     E, NT = batch.n_events, batch.n_tracks
     ctx = pv.Context(device=local, use_graph=1)
     reps = [pv.Tracks.from_batch(batch) for _ in range(N_REPLICAS)]
@@ -355,10 +371,7 @@ def run_ours(args):
     launches = ctx.launch_count() - l0
     clk = clocks.stop()
     per_step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(per_step_ms) / 1e3
-    total_s = _max_over_ranks(dist, total_s)
-    events_all = _sum_over_ranks(dist, float(E * args.steps))
-    value = events_all / total_s
+    events_all, total_s, value = aggregate(dist, float(E * args.steps), sum(per_step_ms) / 1e3)
     kernel_ms = statistics.mean(per_step_ms)
 
     # plain per-step path, same timing

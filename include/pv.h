@@ -60,6 +60,7 @@ extern "C" {
 /* accumulation of the weighted normal equations in the fit */
 #define PV_ACCUM_FP32 0    /* binary32 per lane and across lanes */
 #define PV_ACCUM_KAHAN 1   /* compensated binary32 (error-free transformations) */
+#define PV_ACCUM_FP64 2    /* binary64 sums, reduction and solve (binary32 per-track terms) */
 
 /* execution path */
 #define PV_PATH_FUSED 0    /* bucketed persistent kernels, shared-memory histograms */

@@ -25,7 +25,7 @@ ST_CONVERGED, ST_MAXITER, ST_SINGULAR, ST_REJ_BEAM, ST_REJ_NTRK, ST_ACCEPTED = 1
 EV_SEED_OVERFLOW, EV_BAD_OFFSETS = 1, 4
 ONE = 4096
 MAX_SEEDS = 64
-ACCUM_FP32, ACCUM_KAHAN = 0, 1
+ACCUM_FP32, ACCUM_KAHAN, ACCUM_FP64 = 0, 1, 2
 PATH_FUSED, PATH_PLAIN = 0, 1
 
 EXPORTED = (

@@ -206,7 +206,7 @@ struct pv_ctx {
   // 128-thread find CTAs, 256-thread fit CTAs, occupancy-sized grids)
   pvk::LaunchCfg bucket_cfg[3];
   int find_per_sm[4][3] = {};         // [mode][64/128/256]
-  int fit_per_sm[2][2] = {};          // [kahan][128/256]
+  int fit_per_sm[3][2] = {};          // [accumulation mode][128/256]
   // CUDA graphs of the fused launch, keyed by its arguments
   std::map<std::string, cudaGraphExec_t> graphs;
   cudaStream_t capture_stream = nullptr;
@@ -249,7 +249,9 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
   if (!(nb >= 1.0) || nb > PV_MAX_BINS) return PV_ERR_ARG;
   if (cfg.dip_den <= 0 || cfg.dip_num < 0) return PV_ERR_ARG;
   if (!(cfg.chi2_max > 0.0f) || cfg.max_iter < 0 || cfg.max_iter > 1000) return PV_ERR_ARG;
-  if (cfg.accum_mode != PV_ACCUM_FP32 && cfg.accum_mode != PV_ACCUM_KAHAN) return PV_ERR_ARG;
+  if (cfg.accum_mode != PV_ACCUM_FP32 && cfg.accum_mode != PV_ACCUM_KAHAN &&
+      cfg.accum_mode != PV_ACCUM_FP64)
+    return PV_ERR_ARG;
   if (cfg.path != PV_PATH_FUSED && cfg.path != PV_PATH_PLAIN) return PV_ERR_ARG;
   if (!(cfg.min_integral_pp >= 0.0f) || !(cfg.min_integral_gas >= 0.0f)) return PV_ERR_ARG;
   C->z_min = cfg.z_min;
@@ -368,7 +370,7 @@ pvk::LaunchCfg launch_cfg(const pv_ctx* ctx, int mode, const pv_tracks* t, int f
   long long g = static_cast<long long>(ctx->n_sm) * (per > 0 ? per : 1);
   if (g > t->n_events) g = t->n_events > 0 ? t->n_events : 1;
   L.find_grid = static_cast<int>(g);
-  int fper = ctx->fit_per_sm[ctx->C.accum_mode == PV_ACCUM_KAHAN ? 1 : 0][fit_nt == 128 ? 0 : 1];
+  int fper = ctx->fit_per_sm[ctx->C.accum_mode][fit_nt == 128 ? 0 : 1];
   L.fit_grid = ctx->n_sm * (fper > 0 ? fper : 1);
   return L;
 }
@@ -584,8 +586,8 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
   const int nts[3] = {64, 128, 256};
   for (int mode = 1; mode <= 3; ++mode)
     for (int i = 0; i < 3; ++i) ctx->find_per_sm[mode][i] = pvk::fused_blocks_per_sm(C.nbins, mode, nts[i]);
-  for (int k = 0; k < 2; ++k)
-    for (int i = 0; i < 2; ++i) ctx->fit_per_sm[k][i] = pvk::fit_blocks_per_sm(k == 1, i == 0 ? 128 : 256);
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 2; ++i) ctx->fit_per_sm[k][i] = pvk::fit_blocks_per_sm(k, i == 0 ? 128 : 256);
   for (int b = 0; b < 3; ++b) ctx->bucket_cfg[b] = pvk::LaunchCfg{128, 0, pvk::kFitThreads, 0};
   *out = ctx;
   return PV_OK;

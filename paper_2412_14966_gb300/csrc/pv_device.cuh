@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "pv.h"
 
@@ -468,6 +469,12 @@ __device__ __forceinline__ float group_sum(float v) {
   v += __shfl_xor_sync(0xffffffffu, v, 1);
   return v;
 }
+__device__ __forceinline__ double group_sum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
 __device__ __forceinline__ int group_sum_i(int v) {
   v += __shfl_xor_sync(0xffffffffu, v, 4);
   v += __shfl_xor_sync(0xffffffffu, v, 2);
@@ -519,9 +526,12 @@ __device__ __forceinline__ float group_sum_c(CSum v) {
 // which the shear leaves unchanged, no longer cancels in binary32 when the
 // weighted tracks are nearly parallel.  Step and covariance are mapped back
 // with T = [[1,0,c_x],[0,1,c_y],[0,0,1]] (x = x' + c_x z, C = T C' T^T).
-template <bool kKahan>
+template <int kAccum>
 __device__ void group_fit(const float4* A, const float2* W, int cntk, const Consts& C,
                           VertexOut* out) {
+  // binary32 per-track terms; sums and solve in binary32 (FP32), compensated
+  // binary32 (KAHAN) or binary64 (FP64)
+  using T = typename std::conditional<kAccum == PV_ACCUM_FP64, double, float>::type;
   const int r = threadIdx.x & (kGroup - 1);
   // first shear: W-weighted mean slope of the usable tracks
   float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
@@ -532,19 +542,21 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
     m0 += w2.x; m1 += w2.x * a.z; m2 += w2.y; m3 += w2.y * a.w;
   }
   m0 = group_sum(m0); m1 = group_sum(m1); m2 = group_sum(m2); m3 = group_sum(m3);
-  float cx = m0 > 0.f ? m1 / m0 : 0.f;
-  float cy = m2 > 0.f ? m3 / m2 : 0.f;
-  float ax = 0.f, ay = 0.f, az = 0.f;   // relative to the seed
+  T cx = m0 > 0.f ? static_cast<T>(m1 / m0) : T(0);
+  T cy = m2 > 0.f ? static_cast<T>(m3 / m2) : T(0);
+  T ax = 0, ay = 0, az = 0;           // relative to the seed
   bool done = cntk < 0;
   int status = 0, n_iter = 0;
-  float c2sum = 0, sw = 0, dchi2 = 0;
-  float ix = 0, iy = 0, ux = 0, uy = 0, is = 0;
+  T c2sum = 0, sw = 0, dchi2 = 0;
+  T ix = 0, iy = 0, ux = 0, uy = 0, is = 0;
   int nw = 0;
   for (int it = 1; it <= C.max_iter; ++it) {
-    float v[10];
+    T v[10];
     int cnt_w = 0;
-    const float axp = ax - cx * az, ayp = ay - cy * az;   // sheared position
-    if (kKahan) {
+    const float axp = static_cast<float>(ax - cx * az), ayp = static_cast<float>(ay - cy * az);
+    const float fcx = static_cast<float>(cx), fcy = static_cast<float>(cy);
+    const float faz = static_cast<float>(az);
+    if (kAccum == PV_ACCUM_KAHAN) {
       CSum acc[10];
 #pragma unroll
       for (int q = 0; q < 10; ++q) acc[q] = CSum{0.f, 0.f};
@@ -553,9 +565,9 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
           float4 a = A[s];
           float2 w2 = W[s];
           if (!(w2.x > 0.0f)) continue;
-          float dtx = a.z - cx, dty = a.w - cy;
-          float rx = a.x + az * dtx - axp;
-          float ry = a.y + az * dty - ayp;
+          float dtx = a.z - fcx, dty = a.w - fcy;
+          float rx = a.x + faz * dtx - axp;
+          float ry = a.y + faz * dty - ayp;
           float c2 = rx * rx * w2.x + ry * ry * w2.y;
           float w = 0.f;
           if (c2 < C.chi2_max) { float f = 1.0f - c2 * C.inv_chi2_max; w = f * f; }
@@ -575,26 +587,26 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
       for (int q = 0; q < 10; ++q) v[q] = group_sum_c(acc[q]);
     } else {
 #pragma unroll
-      for (int q = 0; q < 10; ++q) v[q] = 0.f;
+      for (int q = 0; q < 10; ++q) v[q] = T(0);
       if (!done) {
         for (int s = r; s < cntk; s += kGroup) {
           float4 a = A[s];
           float2 w2 = W[s];
           if (!(w2.x > 0.0f)) continue;
-          float dtx = a.z - cx, dty = a.w - cy;
-          float rx = a.x + az * dtx - axp;
-          float ry = a.y + az * dty - ayp;
+          float dtx = a.z - fcx, dty = a.w - fcy;
+          float rx = a.x + faz * dtx - axp;
+          float ry = a.y + faz * dty - ayp;
           float c2 = rx * rx * w2.x + ry * ry * w2.y;
           float w = 0.f;
           if (c2 < C.chi2_max) { float f = 1.0f - c2 * C.inv_chi2_max; w = f * f; }
           if (w > 0.f) {
             float wx = w * w2.x, wy = w * w2.y;
-            v[0] += wx; v[1] += wy;
-            v[2] += wx * dtx; v[3] += wy * dty;
-            v[4] += wx * dtx * dtx + wy * dty * dty;
-            v[5] += wx * rx; v[6] += wy * ry;
-            v[7] += wx * dtx * rx + wy * dty * ry;
-            v[8] += w * c2; v[9] += w;
+            v[0] += T(wx); v[1] += T(wy);
+            v[2] += T(wx * dtx); v[3] += T(wy * dty);
+            v[4] += T(wx * dtx * dtx + wy * dty * dty);
+            v[5] += T(wx * rx); v[6] += T(wy * ry);
+            v[7] += T(wx * dtx * rx + wy * dty * ry);
+            v[8] += T(w * c2); v[9] += T(w);
             ++cnt_w;
           }
         }
@@ -605,31 +617,31 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
     cnt_w = group_sum_i(cnt_w);
     if (!done) {
       // sheared M = [[Sxx,0,-Sxz],[0,Syy,-Syz],[-Sxz,-Syz,Szz]], rhs (bx, by, -bz)
-      float sxx = v[0], syy = v[1], sxz = v[2], syz = v[3], szz = v[4];
-      float bx = v[5], by = v[6], bz = v[7];
+      T sxx = v[0], syy = v[1], sxz = v[2], syz = v[3], szz = v[4];
+      T bx = v[5], by = v[6], bz = v[7];
       n_iter = it;
       c2sum = v[8]; sw = v[9]; nw = cnt_w;
-      float s_ = 0.f;
-      bool ok = sxx > 0.f && syy > 0.f && isfinite(sxx) && isfinite(syy);
+      T s_ = 0;
+      bool ok = sxx > T(0) && syy > T(0) && isfinite(sxx) && isfinite(syy);
       if (ok) {
-        ix = 1.0f / sxx;
-        iy = 1.0f / syy;
+        ix = T(1) / sxx;
+        iy = T(1) / syy;
         ux = sxz * ix;
         uy = syz * iy;
         s_ = szz - sxz * ux - syz * uy;      // Schur complement: the z pivot
         // M_zz of the unsheared matrix, for the relative pivot test
-        float mzz = szz + 2.0f * (cx * sxz + cy * syz) + cx * cx * sxx + cy * cy * syy;
-        ok = s_ > kPivotRel * mzz && isfinite(s_);
+        T mzz = szz + T(2) * (cx * sxz + cy * syz) + cx * cx * sxx + cy * cy * syy;
+        ok = s_ > T(kPivotRel) * mzz && isfinite(s_);
       }
       if (!ok) {
         status = PV_ST_SINGULAR;
-        dchi2 = 0.f;
+        dchi2 = 0;
         done = true;
       } else {
-        is = 1.0f / s_;
-        float dz = (ux * bx + uy * by - bz) * is;
-        float dx = (bx + sxz * dz) * ix;
-        float dy = (by + syz * dz) * iy;
+        is = T(1) / s_;
+        T dz = (ux * bx + uy * by - bz) * is;
+        T dx = (bx + sxz * dz) * ix;
+        T dy = (by + syz * dz) * iy;
         dchi2 = -bx * dx - by * dy + bz * dz;
         ax += dx + cx * dz;
         ay += dy + cy * dz;
@@ -640,7 +652,8 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
         uy += cy;
         cx = ux;
         cy = uy;
-        if (fabsf(dchi2) < C.dchi2_tol && fabsf(dz) < C.dz_tol) {
+        if (fabs(static_cast<double>(dchi2)) < C.dchi2_tol &&
+            fabs(static_cast<double>(dz)) < C.dz_tol) {
           status = PV_ST_CONVERGED;
           done = true;
         } else if (it == C.max_iter) {
@@ -652,18 +665,18 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
   }
   if (cntk < 0) return;
   // C = T C' T^T with ux, uy already mapped back (M_xz/M_xx of the unsheared M)
-  const float uxo = ux, uyo = uy;
-  out->x = ax;       // relative to the seed; the caller adds the seed position
-  out->y = ay;
-  out->z = az;
-  out->cov[0] = ix + uxo * uxo * is;   // xx
-  out->cov[1] = uxo * uyo * is;        // xy
-  out->cov[2] = iy + uyo * uyo * is;   // yy
-  out->cov[3] = uxo * is;              // xz
-  out->cov[4] = uyo * is;              // yz
-  out->cov[5] = is;                    // zz
-  out->chi2 = c2sum + dchi2;
-  out->ndof = 2.0f * sw - 3.0f;
+  const T uxo = ux, uyo = uy;
+  out->x = static_cast<float>(ax);   // relative to the seed; the caller adds the seed position
+  out->y = static_cast<float>(ay);
+  out->z = static_cast<float>(az);
+  out->cov[0] = static_cast<float>(ix + uxo * uxo * is);   // xx
+  out->cov[1] = static_cast<float>(uxo * uyo * is);        // xy
+  out->cov[2] = static_cast<float>(iy + uyo * uyo * is);   // yy
+  out->cov[3] = static_cast<float>(uxo * is);              // xz
+  out->cov[4] = static_cast<float>(uyo * is);              // yz
+  out->cov[5] = static_cast<float>(is);                    // zz
+  out->chi2 = static_cast<float>(c2sum + dchi2);
+  out->ndof = static_cast<float>(T(2) * sw - T(3));
   out->n_tracks = nw;
   out->n_iter = n_iter;
   out->status = status == 0 ? PV_ST_MAXITER : status;

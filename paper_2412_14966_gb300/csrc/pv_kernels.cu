@@ -136,7 +136,7 @@ __device__ __forceinline__ void write_vertex(const Consts& C, const OutPtrs& O, 
 
 // Fit every vertex of one event (block-cooperative; used by the plain path).
 // A, W: per-track fit inputs in vertex order; voff/cnt: vertex ranges.
-template <bool kKahan>
+template <int kAccum>
 __device__ void block_fit_event(const Consts& C, const SeedOut* S, int Ka, const int* voff,
                                 const int* cnt, const float4* A, const float2* W,
                                 const OutPtrs& O, int e) {
@@ -149,7 +149,7 @@ __device__ void block_fit_event(const Consts& C, const SeedOut* S, int Ka, const
     int cntk = has ? cnt[k] : -1;
     int o = has ? voff[k] : 0;
     VertexOut v;
-    group_fit<kKahan>(A + o, W + o, cntk, C, &v);
+    group_fit<kAccum>(A + o, W + o, cntk, C, &v);
     if (has && (lane & 7) == 0) write_vertex(C, O, e, k, S->x[k], S->y[k], S->z[k], v);
   }
 }
@@ -371,7 +371,7 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
 // vertex fit kernel (fused path, stage 2): every 8-lane group fits one vertex
 // of any event; warps take 4 work items at a time.
 
-template <bool kKahan, int FT>
+template <int kAccum, int FT>
 __global__ void __launch_bounds__(FT)
 fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
   const int lane = threadIdx.x & 31;
@@ -409,7 +409,7 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
                      T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, A + s, W + s);
     }
     VertexOut out;
-    group_fit<kKahan>(A, W, cntk, C, &out);
+    group_fit<kAccum>(A, W, cntk, C, &out);
     if (has && r == 0) write_vertex(C, O, w.e, k, xs, ys, zs, out);
   }
 }
@@ -467,7 +467,7 @@ int fused_blocks_per_sm(int nbins, int mode, int nt) {
   return find_blocks_nt<128>(nbins, mode);
 }
 
-template <bool K, int FT>
+template <int K, int FT>
 static int fit_blocks(void) {
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fit_kernel<K, FT>, FT, 0) !=
@@ -476,9 +476,26 @@ static int fit_blocks(void) {
   return blocks;
 }
 
-int fit_blocks_per_sm(bool kahan, int ft) {
-  if (ft == 128) return kahan ? fit_blocks<true, 128>() : fit_blocks<false, 128>();
-  return kahan ? fit_blocks<true, 256>() : fit_blocks<false, 256>();
+template <int FT>
+static int fit_blocks_ft(int accum) {
+  if (accum == PV_ACCUM_KAHAN) return fit_blocks<PV_ACCUM_KAHAN, FT>();
+  if (accum == PV_ACCUM_FP64) return fit_blocks<PV_ACCUM_FP64, FT>();
+  return fit_blocks<PV_ACCUM_FP32, FT>();
+}
+
+int fit_blocks_per_sm(int accum, int ft) {
+  return ft == 128 ? fit_blocks_ft<128>(accum) : fit_blocks_ft<256>(accum);
+}
+
+template <int FT>
+static void launch_fit_ft(int accum, int grid, cudaStream_t st, const Consts& C, const TrackPtrs& T,
+                          const TrackScratch& ws, const OutPtrs& O) {
+  if (accum == PV_ACCUM_KAHAN)
+    fit_kernel<PV_ACCUM_KAHAN, FT><<<grid, FT, 0, st>>>(C, T, ws, O);
+  else if (accum == PV_ACCUM_FP64)
+    fit_kernel<PV_ACCUM_FP64, FT><<<grid, FT, 0, st>>>(C, T, ws, O);
+  else
+    fit_kernel<PV_ACCUM_FP32, FT><<<grid, FT, 0, st>>>(C, T, ws, O);
 }
 
 template <int MODE, int NT>
@@ -508,14 +525,8 @@ cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const Se
   else launch_find<kFindFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
   ++*n_launches;
   if (mode & kFit) {
-    const bool kahan = C.accum_mode == PV_ACCUM_KAHAN;
-    if (L.fit_nt == 128) {
-      if (kahan) fit_kernel<true, 128><<<L.fit_grid, 128, 0, st>>>(C, T, ws, O);
-      else fit_kernel<false, 128><<<L.fit_grid, 128, 0, st>>>(C, T, ws, O);
-    } else {
-      if (kahan) fit_kernel<true, 256><<<L.fit_grid, 256, 0, st>>>(C, T, ws, O);
-      else fit_kernel<false, 256><<<L.fit_grid, 256, 0, st>>>(C, T, ws, O);
-    }
+    if (L.fit_nt == 128) launch_fit_ft<128>(C.accum_mode, L.fit_grid, st, C, T, ws, O);
+    else launch_fit_ft<256>(C.accum_mode, L.fit_grid, st, C, T, ws, O);
     ++*n_launches;
   }
   return cudaGetLastError();
@@ -621,7 +632,7 @@ plain_assoc_kernel(Consts C, TrackPtrs T, OutPtrs O, const int32_t* center, int3
   }
 }
 
-template <bool kKahan>
+template <int kAccum>
 __global__ void __launch_bounds__(256)
 plain_fit_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, int32_t* cid, int32_t* slot,
                  float4* A, float2* W) {
@@ -660,7 +671,7 @@ plain_fit_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, int32_t* cid, in
   __syncthreads();
   block_fit_inputs(T, b0, n, c_e, slot + b0, &S, A + b0, W + b0);
   __syncthreads();
-  block_fit_event<kKahan>(C, &S, K, voff, cnt, A + b0, W + b0, O, e);
+  block_fit_event<kAccum>(C, &S, K, voff, cnt, A + b0, W + b0, O, e);
 }
 
 static int grid_for(int64_t n, int threads) {
@@ -709,9 +720,14 @@ cudaError_t launch_plain_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs
                              const OutPtrs& O, const PlainScratch& ws, cudaStream_t st,
                              int* n_launches) {
   if (C.accum_mode == PV_ACCUM_KAHAN)
-    plain_fit_kernel<true><<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A, ws.W);
+    plain_fit_kernel<PV_ACCUM_KAHAN><<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A,
+                                                                  ws.W);
+  else if (C.accum_mode == PV_ACCUM_FP64)
+    plain_fit_kernel<PV_ACCUM_FP64><<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A,
+                                                                 ws.W);
   else
-    plain_fit_kernel<false><<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A, ws.W);
+    plain_fit_kernel<PV_ACCUM_FP32><<<T.n_events, 256, 0, st>>>(C, T, S, O, ws.cid, ws.slot, ws.A,
+                                                                 ws.W);
   ++*n_launches;
   return cudaGetLastError();
 }

@@ -102,7 +102,7 @@ cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, c
 bool find_block_ok(int nt);
 bool fit_block_ok(int ft);
 int fused_blocks_per_sm(int nbins, int mode, int nt);
-int fit_blocks_per_sm(bool kahan, int ft);
+int fit_blocks_per_sm(int accum, int ft);
 constexpr int kFitThreads = 256;
 
 // Upper bound of the vertices a batch can list: per event at most
