@@ -204,9 +204,11 @@ int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns);
  * real-time loop cannot afford; some applications give all device memory to
  * their own allocator and run with a fixed budget).  Its scratch is a static
  * device array of 8 MiB in the library, held by every GPU that loads the
- * library until the process exits.  A batch needs 40 bytes per track plus 32
- * bytes per vertex slot, where the slots are the smaller of the track count
- * and events x out->capacity: about 155,000 tracks of 160-track events at
+ * library until the process exits.  A batch of n tracks needs 40 bytes per
+ * track plus 32 bytes per entry of four vertex work lists (one per size class
+ * of at least 1, 9, 17 and 33 tracks) holding min(n / 1, S), min(n / 9, S),
+ * min(n / 17, S) and min(n / 33, S) entries, S being the smaller of n and
+ * events x out->capacity: about 140,000 tracks of 160-track events at
  * capacity 64.  Batches needing more are refused with PV_ERR_CAPACITY and a
  * message in pv_last_cuda_error.  The first call on a device looks the array up
  * (cudaGetSymbolAddress); make that first call before any stream capture.

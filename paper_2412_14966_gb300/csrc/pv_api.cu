@@ -62,8 +62,13 @@ size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 struct FusedLayout {
   size_t counter, center, cid, slot, sorted, A, W, work, total;
   int64_t work_cap;
+  int64_t cls_cap[pvk::kWorkClasses];
   FusedLayout(int64_t n, int64_t n_events, int cap) {
-    work_cap = pvk::work_capacity(n, n_events, cap);
+    work_cap = 0;
+    for (int c = 0; c < pvk::kWorkClasses; ++c) {
+      cls_cap[c] = pvk::class_capacity(c, n, n_events, cap);
+      work_cap += cls_cap[c];
+    }
     size_t o = 0;
     counter = o; o += 256;
     A = o; o += round16(sizeof(float4) * n);
@@ -85,7 +90,12 @@ struct FusedLayout {
     s.A = reinterpret_cast<float4*>(b + A);
     s.W = reinterpret_cast<float2*>(b + W);
     s.work = reinterpret_cast<pvk::VertexWork*>(b + work);
-    s.work_cap = static_cast<int>(work_cap);
+    int64_t first = 0;
+    for (int c = 0; c < pvk::kWorkClasses; ++c) {
+      s.cls_base[c] = first;
+      s.cls_cap[c] = static_cast<int>(cls_cap[c]);
+      first += cls_cap[c];
+    }
     s.counters = reinterpret_cast<int*>(b + counter);
     return s;
   }

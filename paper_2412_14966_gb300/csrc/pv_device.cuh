@@ -143,6 +143,57 @@ __device__ __forceinline__ void fill_profile(uint32_t* hist, float zpoca, float 
   }
 }
 
+// Warp-cooperative fill of the profiles of the 32 tracks held by the lanes
+// (one per lane; nb = 0 for a lane without a filled track).  The warp's
+// (track, bin) items are spread over the lanes, so no lane idles while
+// another walks a long window.  Bin j of a window [j0, j1] receives
+// Q_{j+1} - Q_j with Q_{j0} = 0, Q_{j1+1} = ONE and Q_j the quantised CDF at
+// edge j: each lane evaluates the CDF at the left edge of its bin and takes
+// the right edge from the next lane (items of one track sit in consecutive
+// lanes), so a pass covers 31 items and lane 31 only supplies an edge.  The
+// running-max guard of fill_profile is a no-op that is not repeated here: Q is
+// non-decreasing along a window because F is monotone on [-1, 1], every
+// binary32 step of u and F is a monotone rounding, and window edges are at
+// least dz / (sqrt(5) sigma_max) = 0.011 apart in u, far above the rounding
+// error of F.  The histogram is therefore the one fill_profile builds.
+__device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, float sigma,
+                                                   int j0, int nb, const Consts& C) {
+  const int lane = threadIdx.x & 31;
+  float s = __fmul_rn(kSqrt5, sigma);
+  if (s < kSMin) s = 0.0f;
+  const float inv_s = (nb > 1 && s > 0.0f) ? __fdiv_rn(1.0f, s) : 0.0f;
+  int incl = nb;                      // inclusive prefix of the window sizes
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  // 31 items per pass: lane 31 only supplies the left edge of the item after
+  // lane 30's (the first item of the next pass)
+  for (int base = 0; base < total; base += 31) {
+    const int idx = base + lane;
+    int L = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+      if (__shfl_sync(0xffffffffu, incl, L + step - 1) <= idx) L += step;
+    const int o_incl = __shfl_sync(0xffffffffu, incl, L);
+    const int o_nb = __shfl_sync(0xffffffffu, nb, L);
+    const int o_j0 = __shfl_sync(0xffffffffu, j0, L);
+    const float o_z = __shfl_sync(0xffffffffu, zpoca, L);
+    const float o_inv = __shfl_sync(0xffffffffu, inv_s, L);
+    const int i = idx - (o_incl - o_nb);
+    const int j = o_j0 + i;
+    int ql = 0;                       // quantised CDF at the left edge of bin j
+    if (idx < total && i > 0) ql = quant_cdf(__fmul_rn(__fsub_rn(edge_of(j, C), o_z), o_inv));
+    const int qn = __shfl_down_sync(0xffffffffu, ql, 1);
+    const int qr = (i == o_nb - 1) ? kOne : qn;
+    const int w = qr - ql;
+    if (lane < 31 && idx < total && w > 0 && j >= 0 && j < C.nbins)
+      atomicAdd(hist + j, static_cast<uint32_t>(w));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // step (c): proto-clusters, dip splitting in z order, seeds
 
@@ -398,28 +449,29 @@ __device__ int block_associate(const CenterT* center, CidT* cid, int n, SeedOut*
     if (!*flag) break;
   }
   int ka = s_ka;
-  // compact survivors in z order (alive is increasing)
+  // compact survivors in z order.  alive is increasing (alive[q] >= q), so
+  // the first 32 survivors can be moved once all of them are read, and the
+  // rest only read entries at or above 32, which the first half leaves alone.
   if (tid < 32) {
-    int lo[2], hi[2], bn[2];
-    float z[2], x[2], y[2];
-    uint32_t nm[2], ni[2], np[2];
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
-      int q = tid + 32 * h;
+      const int q = tid + 32 * h;
+      int lo = 0, hi = 0, bn = 0;
+      float z = 0.f, x = 0.f, y = 0.f;
+      uint32_t nm = 0, ni = 0, np = 0;
       if (q < ka) {
-        int k = alive[q];
-        lo[h] = S->lo[k]; hi[h] = S->hi[k]; bn[h] = S->bin[k];
-        z[h] = S->z[k]; x[h] = S->x[k]; y[h] = S->y[k];
-        nm[h] = S->nm[k]; ni[h] = S->ni[k]; np[h] = S->np[k];
+        const int k = alive[q];
+        lo = S->lo[k]; hi = S->hi[k]; bn = S->bin[k];
+        z = S->z[k]; x = S->x[k]; y = S->y[k];
+        nm = S->nm[k]; ni = S->ni[k]; np = S->np[k];
       }
-    }
-    __syncwarp();
-    for (int h = 0; h < 2; ++h) {
-      int q = tid + 32 * h;
+      __syncwarp();
       if (q < ka) {
-        S->lo[q] = lo[h]; S->hi[q] = hi[h]; S->bin[q] = bn[h];
-        S->z[q] = z[h]; S->x[q] = x[h]; S->y[q] = y[h];
-        S->nm[q] = nm[h]; S->ni[q] = ni[h]; S->np[q] = np[h];
+        S->lo[q] = lo; S->hi[q] = hi; S->bin[q] = bn;
+        S->z[q] = z; S->x[q] = x; S->y[q] = y;
+        S->nm[q] = nm; S->ni[q] = ni; S->np[q] = np;
       }
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -516,7 +568,10 @@ __device__ __forceinline__ float group_sum_c(CSum v) {
 // Fit of one vertex per 8-lane group.  Every lane of the warp must call it
 // (shuffles); lanes of groups without a vertex pass cntk = -1.  Track s of the
 // vertex (s = 0 .. cntk-1, in track-index order) is handled by lane s mod 8 of
-// the group.  The result lands in *out on every lane of the group.
+// the group, which finds its j-th track (s = r + 8 j) at A[j * stride],
+// W[j * stride] (the lane's own fit inputs: in global memory in vertex order,
+// or in the lane's shared-memory slots).  The result lands in *out on every
+// lane of the group.
 //
 // Each iteration solves the normal equations in sheared coordinates
 // x' = x - c_x z, y' = y - c_y z, with c the weighted mean slope of the
@@ -527,17 +582,17 @@ __device__ __forceinline__ float group_sum_c(CSum v) {
 // weighted tracks are nearly parallel.  Step and covariance are mapped back
 // with T = [[1,0,c_x],[0,1,c_y],[0,0,1]] (x = x' + c_x z, C = T C' T^T).
 template <int kAccum>
-__device__ void group_fit(const float4* A, const float2* W, int cntk, const Consts& C,
-                          VertexOut* out) {
+__device__ void group_fit(const float4* A, const float2* W, int stride, int cntk,
+                          const Consts& C, VertexOut* out) {
   // binary32 per-track terms; sums and solve in binary32 (FP32), compensated
   // binary32 (KAHAN) or binary64 (FP64)
   using T = typename std::conditional<kAccum == PV_ACCUM_FP64, double, float>::type;
   const int r = threadIdx.x & (kGroup - 1);
   // first shear: W-weighted mean slope of the usable tracks
   float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-  for (int s = r; s < cntk; s += kGroup) {
-    float4 a = A[s];
-    float2 w2 = W[s];
+  for (int s = r, q = 0; s < cntk; s += kGroup, q += stride) {
+    float4 a = A[q];
+    float2 w2 = W[q];
     if (!(w2.x > 0.0f)) continue;
     m0 += w2.x; m1 += w2.x * a.z; m2 += w2.y; m3 += w2.y * a.w;
   }
@@ -561,9 +616,9 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
 #pragma unroll
       for (int q = 0; q < 10; ++q) acc[q] = CSum{0.f, 0.f};
       if (!done) {
-        for (int s = r; s < cntk; s += kGroup) {
-          float4 a = A[s];
-          float2 w2 = W[s];
+        for (int s = r, q = 0; s < cntk; s += kGroup, q += stride) {
+          float4 a = A[q];
+          float2 w2 = W[q];
           if (!(w2.x > 0.0f)) continue;
           float dtx = a.z - fcx, dty = a.w - fcy;
           float rx = a.x + faz * dtx - axp;
@@ -589,9 +644,9 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
 #pragma unroll
       for (int q = 0; q < 10; ++q) v[q] = T(0);
       if (!done) {
-        for (int s = r; s < cntk; s += kGroup) {
-          float4 a = A[s];
-          float2 w2 = W[s];
+        for (int s = r, q = 0; s < cntk; s += kGroup, q += stride) {
+          float4 a = A[q];
+          float2 w2 = W[q];
           if (!(w2.x > 0.0f)) continue;
           float dtx = a.z - fcx, dty = a.w - fcy;
           float rx = a.x + faz * dtx - axp;
@@ -652,8 +707,8 @@ __device__ void group_fit(const float4* A, const float2* W, int cntk, const Cons
         uy += cy;
         cx = ux;
         cy = uy;
-        if (fabs(static_cast<double>(dchi2)) < C.dchi2_tol &&
-            fabs(static_cast<double>(dz)) < C.dz_tol) {
+        const T adchi2 = dchi2 < T(0) ? -dchi2 : dchi2, adz = dz < T(0) ? -dz : dz;
+        if (adchi2 < static_cast<T>(C.dchi2_tol) && adz < static_cast<T>(C.dz_tol)) {
           status = PV_ST_CONVERGED;
           done = true;
         } else if (it == C.max_iter) {

@@ -134,6 +134,20 @@ __device__ __forceinline__ void write_vertex(const Consts& C, const OutPtrs& O, 
   if (O.status) O.status[q] = st;
 }
 
+// A seed without tracks gets the result of an empty fit at its seed
+// position.  Rare, and kept out of line so that its registers do not count
+// against the find kernel's occupancy.
+__device__ __noinline__ void write_empty_vertex(const Consts& C, const OutPtrs& O,
+                                                const SeedOut* S, int e, int k) {
+  float xs = S->x[k], ys = S->y[k], zs = S->z[k];
+  if (S->bin[k] >= 0) {
+    zs = seed_z_from(S->nm[k], S->ni[k], S->np[k], S->bin[k], C);
+    xs = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
+    ys = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
+  }
+  write_vertex(C, O, e, k, xs, ys, zs, empty_fit(C));
+}
+
 // Fit every vertex of one event (block-cooperative; used by the plain path).
 // A, W: per-track fit inputs in vertex order; voff/cnt: vertex ranges.
 template <int kAccum>
@@ -149,7 +163,8 @@ __device__ void block_fit_event(const Consts& C, const SeedOut* S, int Ka, const
     int cntk = has ? cnt[k] : -1;
     int o = has ? voff[k] : 0;
     VertexOut v;
-    group_fit<kAccum>(A + o, W + o, cntk, C, &v);
+    const int r = lane & (kGroup - 1);
+    group_fit<kAccum>(A + o + r, W + o + r, kGroup, cntk, C, &v);
     if (has && (lane & 7) == 0) write_vertex(C, O, e, k, S->x[k], S->y[k], S->z[k], v);
   }
 }
@@ -210,19 +225,25 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
     for (int i = tid; i < C.ntiles * 32; i += NT) hist[i] = 0u;
   }
   if (tid < kTileWords) tmask[tid] = 0u;
+  if (tid == 0) misc[0] = atomicAdd(G.counters, 1);
   __syncthreads();
 
   for (int iter = 0;; ++iter) {
-    if (tid == 0) misc[iter & 1] = atomicAdd(G.counters, 1);
-    __syncthreads();
     const int e = misc[iter & 1];
     if (e >= T.n_events) break;
+    // the next event is claimed while this one runs, by the last warp (the
+    // one with the fewest tracks); the barrier that ends the iteration
+    // publishes it
+    int e_next = 0;
+    if (tid == NT - 1) e_next = atomicAdd(G.counters, 1);
     const int64_t b0 = T.off[e], b1 = T.off[e + 1];
     if (offsets_bad(b0, b1, T.n_tracks)) {
       if (tid == 0) {
         O.n_per_event[e] = 0;
         if (O.event_status) O.event_status[e] = PV_EV_BAD_OFFSETS;
       }
+      if (tid == NT - 1) misc[(iter + 1) & 1] = e_next;
+      __syncthreads();
       continue;   // uniform: every thread read the same offsets
     }
     const int n = static_cast<int>(b1 - b0);
@@ -233,12 +254,21 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
     int Ka = 0;
 
     if (MODE & kFind) {
-      // (a) + (b): extrapolate, mark tiles, fill the shared histogram
-      for (int t = tid; t < n; t += NT) {
-        const int64_t i = b0 + t;
-        Prep p = prepare_track(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i], T.cxtx[i],
-                               T.ctxtx[i], C);
-        center[t] = p.filled ? p.center : -1;
+      // (a) + (b): extrapolate, mark tiles, fill the shared histogram (one
+      // track per lane, then the warp's (track, bin) items spread over lanes)
+      for (int t0 = warp * 32; t0 < n; t0 += NT) {
+        const int t = t0 + lane;
+        Prep p;
+        p.filled = false;
+        p.zpoca = p.sigma = 0.0f;
+        p.j0 = 0;
+        p.j1 = -1;
+        if (t < n) {
+          const int64_t i = b0 + t;
+          p = prepare_track(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i], T.cxtx[i],
+                            T.ctxtx[i], C);
+          center[t] = p.filled ? p.center : -1;
+        }
         if (p.filled) {
           int q0 = (p.j0 < 0 ? 0 : p.j0) >> 5;
           int q1 = (p.j1 >= C.nbins ? C.nbins - 1 : p.j1) >> 5;
@@ -246,9 +276,10 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
             uint32_t bit = 1u << (q & 31);
             if (!(tmask[q >> 5] & bit)) atomicOr(tmask + (q >> 5), bit);
           }
-          fill_profile(hist, p.zpoca, p.sigma, p.j0, p.j1, C);
         }
+        warp_fill_profiles(hist, p.zpoca, p.sigma, p.j0, p.filled ? p.j1 - p.j0 + 1 : 0, C);
       }
+      if (tid == NT - 1) misc[(iter + 1) & 1] = e_next;
       __syncthreads();
       // (c): seeds from the touched tiles (warp 0)
       if (warp == 0) {
@@ -306,6 +337,7 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       }
       if (tid == 0 && O.n_per_event != SP.n_per_event) O.n_per_event[e] = K;
       Ka = K;
+      if (tid == NT - 1) misc[(iter + 1) & 1] = e_next;
       __syncthreads();
     }
 
@@ -317,21 +349,38 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       if (warp == 0) {
         warp_slots(cid, n, base, slot);
       } else if (warp == 1) {
+        // one work item per vertex with tracks, in the list of its size class
         const unsigned lt = (1u << lane) - 1u;
-        const bool h0 = lane < Ka && cnt[lane] > 0;
-        const bool h1 = lane + 32 < Ka && cnt[lane + 32] > 0;
-        const unsigned m0 = __ballot_sync(0xffffffffu, h0);
-        const unsigned m1 = __ballot_sync(0xffffffffu, h1);
+        const int c0 = (lane < Ka && cnt[lane] > 0) ? work_class(cnt[lane]) : -1;
+        const int c1 = (lane + 32 < Ka && cnt[lane + 32] > 0) ? work_class(cnt[lane + 32]) : -1;
+        // per class: lane c reserves the class's entries (one round trip for
+        // all classes), then each vertex takes its rank within its class
+        int mine = 0;
+#pragma unroll 1
+        for (int c = 0; c < kWorkClasses; ++c) {
+          const int k = __popc(__ballot_sync(0xffffffffu, c0 == c)) +
+                        __popc(__ballot_sync(0xffffffffu, c1 == c));
+          if (lane == c) mine = k;
+        }
         int wb = 0;
-        if (lane == 0) wb = atomicAdd(G.counters + 1, __popc(m0) + __popc(m1));
-        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (lane < kWorkClasses && mine > 0) wb = atomicAdd(G.counters + 1 + lane, mine);
+        int i0 = 0, i1 = 0;
+#pragma unroll 1
+        for (int c = 0; c < kWorkClasses; ++c) {
+          const unsigned m0 = __ballot_sync(0xffffffffu, c0 == c);
+          const unsigned m1 = __ballot_sync(0xffffffffu, c1 == c);
+          const int bc = __shfl_sync(0xffffffffu, wb, c);
+          if (c0 == c) i0 = bc + __popc(m0 & lt);
+          if (c1 == c) i1 = bc + __popc(m0) + __popc(m1 & lt);
+        }
+#pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           const int k = lane + 32 * h;
           if (k >= Ka) continue;
-          const unsigned m = h ? m1 : m0;
-          const int idx = wb + (h ? __popc(m0) : 0) + __popc(m & lt);
-          if (cnt[k] > 0) {
-            if (idx < G.work_cap) {
+          const int cl = h ? c1 : c0;
+          const int idx = h ? i1 : i0;
+          if (cl >= 0) {
+            if (idx < class_pick(G.cls_cap, cl)) {
               VertexWork w;
               w.off = static_cast<int>(b0 + voff[k]);
               w.e = e;
@@ -345,16 +394,10 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
                 w.c = __float_as_uint(S->z[k]);
               }
               w.pad = 0;
-              G.work[idx] = w;
+              G.work[class_pick(G.cls_base, cl) + idx] = w;
             }
           } else {
-            float xs = S->x[k], ys = S->y[k], zs = S->z[k];
-            if (S->bin[k] >= 0) {
-              zs = seed_z_from(S->nm[k], S->ni[k], S->np[k], S->bin[k], C);
-              xs = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
-              ys = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
-            }
-            write_vertex(C, O, e, k, xs, ys, zs, empty_fit(C));
+            write_empty_vertex(C, O, S, e, k);
           }
         }
       }
@@ -364,6 +407,7 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
         if (c >= 0) G.sorted[b0 + slot[t]] = static_cast<int32_t>(b0 + t);
       }
     }
+    __syncthreads();   // shared state is reused by the next event
   }
 }
 
@@ -374,19 +418,33 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
 template <int kAccum, int FT>
 __global__ void __launch_bounds__(FT)
 fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
+  // kLaneSlots fit inputs per thread: slot j of thread i at [j * FT + i]
+  __shared__ float4 sA[kLaneSlots * FT];
+  __shared__ float2 sW[kLaneSlots * FT];
   const int lane = threadIdx.x & 31;
   const int r = lane & (kGroup - 1);
-  const int n = min(G.counters[1], G.work_cap);
+  // the classes' listed vertices, largest class first
+  static_assert(kWorkClasses == 4, "class selection below");
+  const int n0 = min(G.counters[1], G.cls_cap[0]), n1 = min(G.counters[2], G.cls_cap[1]);
+  const int n2 = min(G.counters[3], G.cls_cap[2]), n3 = min(G.counters[4], G.cls_cap[3]);
+  const int n = n0 + n1 + n2 + n3;
   for (;;) {
     int b = 0;
-    if (lane == 0) b = atomicAdd(G.counters + 2, kGroupsPerWarp);
+    if (lane == 0) b = atomicAdd(G.counters + 1 + kWorkClasses, kGroupsPerWarp);
     b = __shfl_sync(0xffffffffu, b, 0);
     if (b >= n) break;
     const int v = b + (lane >> 3);
     const bool has = v < n;
     VertexWork w;
     w.off = 0; w.e = 0; w.kc = 0; w.bin = -1; w.a = w.b = w.c = 0u; w.pad = 0;
-    if (has) w = G.work[v];
+    if (has) {
+      long long q;
+      if (v < n3) q = G.cls_base[3] + v;
+      else if (v < n3 + n2) q = G.cls_base[2] + (v - n3);
+      else if (v < n3 + n2 + n1) q = G.cls_base[1] + (v - n3 - n2);
+      else q = G.cls_base[0] + (v - n3 - n2 - n1);
+      w = G.work[q];
+    }
     const int k = w.kc & 0xff;
     const int cntk = has ? (w.kc >> 8) : -1;
     // seed position: given, or z_seed from the bins around the maximum
@@ -399,17 +457,28 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
       xs = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
       ys = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
     }
-    // this lane's tracks: fit inputs relative to the seed (read back below
-    // by the same lane only)
-    float4* A = G.A + w.off;
-    float2* W = G.W + w.off;
-    for (int s = r; s < cntk; s += kGroup) {
+    // this lane's tracks: fit inputs relative to the seed, read back by the
+    // same lane only, so they live in the lane's shared-memory slots (strided
+    // by the block size: conflict-free) unless the vertex is too large
+    float4* A;
+    float2* W;
+    int stride;
+    if (cntk <= kGroup * kLaneSlots) {
+      A = sA + threadIdx.x;
+      W = sW + threadIdx.x;
+      stride = FT;
+    } else {
+      A = G.A + w.off + r;
+      W = G.W + w.off + r;
+      stride = kGroup;
+    }
+    for (int s = r, q = 0; s < cntk; s += kGroup, q += stride) {
       const int t = G.sorted[w.off + s];
       make_fit_track(T.x[t], T.y[t], T.z[t], T.tx[t], T.ty[t], T.cxx[t], T.cxtx[t], T.ctxtx[t],
-                     T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, A + s, W + s);
+                     T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, A + q, W + q);
     }
     VertexOut out;
-    group_fit<kAccum>(A, W, cntk, C, &out);
+    group_fit<kAccum>(A, W, stride, cntk, C, &out);
     if (has && r == 0) write_vertex(C, O, w.e, k, xs, ys, zs, out);
   }
 }
@@ -518,7 +587,7 @@ cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const Se
                          const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
                          cudaStream_t st, int* n_launches) {
   size_t sm = fused_smem_bytes(C.nbins, mode);
-  cudaError_t err = cudaMemsetAsync(ws.counters, 0, 4 * sizeof(int), st);
+  cudaError_t err = cudaMemsetAsync(ws.counters, 0, kCounterInts * sizeof(int), st);
   if (err != cudaSuccess) return err;
   if (mode == kFind) launch_find<kFind>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
   else if (mode == kFit) launch_find<kFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);

@@ -45,6 +45,16 @@ struct VertexWork {
   int pad;
 };
 
+// The vertex work list is split by size class (tracks per vertex: 1-8,
+// 9-16, 17-32, 33 and more) so that the four vertices a warp fits together
+// need similar numbers of passes over their tracks; the fit kernel takes the
+// classes from the largest down.
+constexpr int kWorkClasses = 4;
+__host__ __device__ inline int work_class(int cnt) {
+  return cnt <= 8 ? 0 : (cnt <= 16 ? 1 : (cnt <= 32 ? 2 : 3));
+}
+constexpr int kClassMinTracks[kWorkClasses] = {1, 9, 17, 33};
+
 // Global scratch of the fused path (indexed by the global track index).
 struct TrackScratch {
   int32_t* center;      // per track, events above kSmallCap tracks
@@ -53,10 +63,25 @@ struct TrackScratch {
   int32_t* sorted;      // per track: global track indices in vertex order
   float4* A;            // per track: fit inputs in vertex order
   float2* W;
-  VertexWork* work;     // vertex work list
-  int work_cap;         // its capacity: events x vertex capacity per event
-  int* counters;        // [0] next event, [1] vertices listed, [2] next vertex to fit
+  VertexWork* work;     // vertex work lists, one region per size class
+  long long cls_base[kWorkClasses];   // first entry of each class's region
+  int cls_cap[kWorkClasses];    // its capacity
+  int* counters;        // [0] next event, [1 + c] vertices listed in class c,
+                        // [1 + kWorkClasses] next vertex to fit
 };
+constexpr int kCounterInts = 8;
+
+// fit inputs each fit-kernel thread keeps in shared memory: vertices of up to
+// 8 x kLaneSlots tracks are fitted from shared memory, larger ones from the
+// global scratch (24 bytes per slot: 24 KB per 128-thread block)
+constexpr int kLaneSlots = 8;
+
+// a[c] with constant indices only (a kernel parameter indexed at run time
+// would be copied to local memory)
+template <typename V>
+__host__ __device__ __forceinline__ V class_pick(const V (&a)[kWorkClasses], int c) {
+  return c == 0 ? a[0] : (c == 1 ? a[1] : (c == 2 ? a[2] : a[3]));
+}
 
 enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3 };
 
@@ -111,6 +136,14 @@ inline long long work_capacity(long long n_tracks, long long n_events, int cap) 
   long long c = cap < pvdev::kMaxSeeds ? cap : pvdev::kMaxSeeds;
   long long by_events = n_events * c;
   return by_events < n_tracks ? by_events : n_tracks;
+}
+
+// Upper bound of the vertices of size class c: a vertex of the class has at
+// least kClassMinTracks[c] tracks.
+inline long long class_capacity(int c, long long n_tracks, long long n_events, int cap) {
+  long long all = work_capacity(n_tracks, n_events, cap);
+  long long by_tracks = n_tracks / kClassMinTracks[c];
+  return by_tracks < all ? by_tracks : all;
 }
 
 int fused_blocks_per_sm(int nbins, int mode);

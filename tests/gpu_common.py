@@ -62,10 +62,13 @@ def _first_diff(a, b):
     return f"first difference at {d[:5]}: {a[d[:5]]} vs {b[d[:5]]}" if len(d) else ""
 
 
-def fit_mismatches(gpu: dict, ref: dict, n_seeds: np.ndarray):
+def fit_mismatches(gpu: dict, ref: dict, n_seeds: np.ndarray, cond=None):
     """Per-vertex comparison.  Returns (list of (e, k) whose iteration counts
-    differ, dict of worst errors over vertices with equal counts)."""
-    worst = {"xy": 0.0, "z": 0.0, "cov": 0.0}
+    differ, dict of worst errors over vertices with equal counts).  A
+    covariance outside TOL_COV is accepted only for an ill-conditioned vertex
+    (``cond`` = (batch, found, params); see cov_spread) within ILL_FACTOR times
+    the oracle's own spread; those vertices are listed under "ill"."""
+    worst = {"xy": 0.0, "z": 0.0, "cov": 0.0, "ill": []}
     differ = []
     for e in range(len(n_seeds)):
         for k in range(n_seeds[e]):
@@ -80,7 +83,13 @@ def fit_mismatches(gpu: dict, ref: dict, n_seeds: np.ndarray):
             worst["xy"] = max(worst["xy"], abs(gpu["x"][e, k] - ref["x"][e, k]),
                               abs(gpu["y"][e, k] - ref["y"][e, k]))
             worst["z"] = max(worst["z"], abs(gpu["z"][e, k] - ref["z"][e, k]))
-            worst["cov"] = max(worst["cov"], cov_error(gpu["cov"][e, k], ref["cov"][e, k]))
+            ce = cov_error(gpu["cov"][e, k], ref["cov"][e, k])
+            if ce >= TOL_COV and cond is not None:
+                spread = cov_spread(*cond, e, k)
+                assert spread >= TOL_COV / ILL_FACTOR and ce < ILL_FACTOR * spread, (e, k, ce, spread)
+                worst["ill"].append((e, k, ce, spread))
+            else:
+                worst["cov"] = max(worst["cov"], ce)
             assert gs == rs, (e, k, gs, rs, gpu["n_tracks"][e, k], ref["n_tracks"][e, k])
             assert gpu["n_tracks"][e, k] == ref["n_tracks"][e, k], (e, k)
     return differ, worst
@@ -95,11 +104,51 @@ def cov_error(g, r) -> float:
     return err
 
 
-def assert_fit_close(gpu, ref, n_seeds, tight_pair=None):
+# An ill-conditioned covariance: one whose oracle value moves by more than
+# TOL_COV / ILL_FACTOR when the vertex's binary32 track inputs move by one ulp.
+# Binary32 per-track arithmetic cannot pin such a covariance to TOL_COV (a
+# track with chi2 just below chi2_max, whose Tukey weight (1 - chi2/chi2_max)^2
+# carries most of the z information, is the typical case); it is compared at
+# ILL_FACTOR times that spread instead.
+ILL_FACTOR = 10.0
+
+
+def vertex_tracks(batch, found: dict, e: int, k: int) -> dict:
+    b0, b1 = int(batch.offsets[e]), int(batch.offsets[e + 1])
+    idx = b0 + np.nonzero(found["track_cluster"][b0:b1] == k)[0]
+    return {kk: vv[idx] for kk, vv in batch.tracks.items()}
+
+
+def cov_spread(batch, found: dict, p, e: int, k: int, n_draw: int = 8) -> float:
+    """Largest change of the oracle's covariance of vertex (e, k) (cov_error
+    measure) over n_draw refits whose binary32 track inputs are each moved by
+    one ulp in a random direction."""
+    t = vertex_tracks(batch, found, e, k)
+    seed = (found["x"][e, k], found["y"][e, k], found["z"][e, k])
+    base = oracle.fit_tracks(t, seed, p)
+    rng = np.random.default_rng(1000 * e + k)
+    worst = 0.0
+    for _ in range(n_draw):
+        tp = {}
+        for kk, v in t.items():
+            v = np.asarray(v, np.float32)
+            up = rng.integers(0, 2, v.shape).astype(bool)
+            tp[kk] = np.where(up, np.nextafter(v, np.float32(np.inf)),
+                              np.nextafter(v, np.float32(-np.inf))).astype(np.float32)
+        r = oracle.fit_tracks(tp, seed, p)
+        if r["status"] & oracle.SINGULAR:
+            continue
+        worst = max(worst, cov_error(r["cov"], base["cov"]))
+    return worst
+
+
+def assert_fit_close(gpu, ref, n_seeds, tight_pair=None, cond=None):
     """Tolerances on every vertex whose iteration counts agree; the others are
     refitted on both sides to full convergence (``tight_pair`` = callable
-    returning (gpu_tight, ref_tight)) and compared there."""
-    differ, worst = fit_mismatches(gpu, ref, n_seeds)
+    returning (gpu_tight, ref_tight)) and compared there.  ``cond`` =
+    (batch, found, params) enables the ill-conditioned rule of
+    fit_mismatches."""
+    differ, worst = fit_mismatches(gpu, ref, n_seeds, cond)
     assert worst["xy"] < TOL_XY, worst
     assert worst["z"] < TOL_Z, worst
     assert worst["cov"] < TOL_COV, worst

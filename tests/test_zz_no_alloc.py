@@ -36,13 +36,16 @@ def _compare(out: dict, ref: dict, batch):
 
 
 def _scratch_bytes(batch, capacity=64):
-    """Scratch a batch needs: 40 B per track and 32 B per vertex slot (the
-    smaller of tracks and events x capacity), each array 16-byte aligned."""
+    """Scratch a batch needs: 40 B per track, and 32 B per entry of the four
+    vertex work lists (size classes of at least 1, 9, 17 and 33 tracks; each
+    holds at most min(tracks / that minimum, slots), slots being the smaller of
+    tracks and events x capacity), each array 16-byte aligned."""
     def r16(v):
         return (v + 15) // 16 * 16
     n = batch.n_tracks
     slots = min(n, batch.n_events * capacity)
-    return 256 + r16(16 * n) + r16(8 * n) + 4 * r16(4 * n) + r16(32 * slots)
+    work = sum(min(n // m, slots) for m in (1, 9, 17, 33))
+    return 256 + r16(16 * n) + r16(8 * n) + 4 * r16(4 * n) + r16(32 * work)
 
 
 def test_static_scratch_entry_point_matches_allocating_one():
