@@ -203,18 +203,26 @@ struct SeedOut {   // shared-memory seed table of one event
   uint32_t nm[kMaxSeeds], ni[kMaxSeeds], np[kMaxSeeds];   // N[bin-1], N[bin], N[bin+1]
 };
 
-// Walk proto-cluster [a, b] of N; calls emit(lo, hi, integral) per piece in
-// z order.  Splits at the leftmost bin of a significant minimum between the
-// running maximum of the open piece (L) and the next maximum (R) if both the
-// piece [s, m] and the rest [m+1, b] hold the minimal integral.
+// Walk proto-cluster [a, b] of N; calls emit(lo, hi, integral, im) per piece
+// in z order, im being the piece's maximum bin (lowest index on ties).
+// Splits at the leftmost bin of a significant minimum between the running
+// maximum of the open piece (L, first reached at bin iL) and the next maximum
+// (R, first reached at bin kf) if both the piece [s, m] and the rest
+// [m+1, b] hold the minimal integral.  A piece's maximum is L: values fall
+// after it up to the split point, and the piece after a split starts with
+// the minimum's plateau and the ascent to R.
 template <class Emit>
 __host__ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t total,
                                     const Consts& C, Emit&& emit) {
   int s = a;
   uint64_t pre_s = 0;                 // sum over [a, s)
-  int top = a;
+  int top = a, iL = a;
   uint64_t pre = N[a];                // sum over [a, top]
-  while (top < b && N[top + 1] >= N[top]) { ++top; pre += N[top]; }
+  while (top < b && N[top + 1] >= N[top]) {
+    ++top;
+    pre += N[top];
+    if (N[top] > N[top - 1]) iL = top;
+  }
   uint32_t L = N[top];
   while (top < b) {
     int j = top, m = top;
@@ -225,9 +233,13 @@ __host__ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t to
       if (N[j] < N[j - 1]) { m = j; pre_m = pre_j; }
     }
     if (j == b) break;
-    int k = j;
+    int k = j, kf = j;
     uint64_t pre_k = pre_j;
-    while (k < b && N[k + 1] >= N[k]) { ++k; pre_k += N[k]; }
+    while (k < b && N[k + 1] >= N[k]) {
+      ++k;
+      pre_k += N[k];
+      if (N[k] > N[k - 1]) kf = k;
+    }
     uint32_t R = N[k];
     uint32_t lower = L < R ? L : R;
     bool split = false;
@@ -236,31 +248,25 @@ __host__ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t to
       if (pre_m - pre_s >= T && total - pre_m >= T) split = true;
     }
     if (split) {
-      emit(s, m, pre_m - pre_s);
+      emit(s, m, pre_m - pre_s, iL);
       s = m + 1;
       pre_s = pre_m;
       L = R;
+      iL = kf;
     } else if (R > L) {
       L = R;
+      iL = kf;
     }
     top = k;
     pre = pre_k;
   }
-  emit(s, b, total - pre_s);
+  emit(s, b, total - pre_s, iL);
 }
 
-__host__ __device__ __forceinline__ int argmax_bins(const uint32_t* N, int lo, int hi) {
-  int best = lo;
-  uint32_t bv = N[lo];
-  for (int i = lo + 1; i <= hi; ++i)
-    if (N[i] > bv) { bv = N[i]; best = i; }
-  return best;
-}
-
-__host__ __device__ __forceinline__ bool keep_piece(const uint32_t* N, int lo, int hi,
-                                                    uint64_t integral, const Consts& C, int* im) {
-  *im = argmax_bins(N, lo, hi);
-  uint64_t T = (*im < C.gas_bin) ? C.t_gas : C.t_pp;
+// A piece is a seed cluster if it holds the minimal integral of the region of
+// its maximum bin im.
+__host__ __device__ __forceinline__ bool keep_piece(uint64_t integral, int im, const Consts& C) {
+  uint64_t T = (im < C.gas_bin) ? C.t_gas : C.t_pp;
   return integral >= T;
 }
 
@@ -297,8 +303,24 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
   int n_seeds = 0;
   int n_starts = 0, n_ends = 0, n_done = 0;
 
+  auto put = [&](int pos, int lo, int hi, int im) {
+    const uint32_t nm = bin_or_zero(N, im - 1, C), ni = N[im], np = bin_or_zero(N, im + 1, C);
+    S->lo[pos] = lo;
+    S->hi[pos] = hi;
+    S->bin[pos] = im;
+    S->nm[pos] = nm;
+    S->ni[pos] = ni;
+    S->np[pos] = np;
+    if (kSeedZ) {
+      float zs = seed_z_from(nm, ni, np, im, C);
+      S->z[pos] = zs;
+      S->x[pos] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
+      S->y[pos] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
+    }
+  };
   auto process = [&](int count) {
-    // lane j walks proto-cluster n_done + j (pass 1 counts kept pieces)
+    // lane j walks proto-cluster n_done + j, counting the kept pieces and
+    // keeping the first one; only a lane with several kept pieces walks again
     int a = 0, b = -1;
     uint64_t total = 0;
     if (lane < count) {
@@ -310,11 +332,13 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     // one below the smaller threshold yields no seed: skip its walk
     const uint64_t t_min = C.t_pp < C.t_gas ? C.t_pp : C.t_gas;
     const bool walk = lane < count && total >= t_min;
-    int kept = 0;
+    int kept = 0, lo1 = 0, hi1 = 0, im1 = 0;
     if (walk) {
-      split_walk(N, a, b, total, C, [&](int lo, int hi, uint64_t integral) {
-        int im;
-        if (keep_piece(N, lo, hi, integral, C, &im)) ++kept;
+      split_walk(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
+        if (keep_piece(integral, im, C)) {
+          if (kept == 0) { lo1 = lo; hi1 = hi; im1 = im; }
+          ++kept;
+        }
       });
     }
     int incl = kept;
@@ -324,26 +348,12 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     }
     int n_kept = __shfl_sync(0xffffffffu, incl, 31);
     int pos = n_seeds + incl - kept;
-    if (walk && kept > 0 && pos < cap) {
-      split_walk(N, a, b, total, C, [&](int lo, int hi, uint64_t integral) {
-        int im;
-        if (keep_piece(N, lo, hi, integral, C, &im)) {
-          if (pos < cap) {
-            const uint32_t nm = bin_or_zero(N, im - 1, C), ni = N[im],
-                           np = bin_or_zero(N, im + 1, C);
-            S->lo[pos] = lo;
-            S->hi[pos] = hi;
-            S->bin[pos] = im;
-            S->nm[pos] = nm;
-            S->ni[pos] = ni;
-            S->np[pos] = np;
-            if (kSeedZ) {
-              float zs = seed_z_from(nm, ni, np, im, C);
-              S->z[pos] = zs;
-              S->x[pos] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
-              S->y[pos] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
-            }
-          }
+    if (kept == 1 && pos < cap) {
+      put(pos, lo1, hi1, im1);
+    } else if (kept > 1 && pos < cap) {
+      split_walk(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
+        if (keep_piece(integral, im, C)) {
+          if (pos < cap) put(pos, lo, hi, im);
           ++pos;
         }
       });
@@ -352,6 +362,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     n_done += count;
     __syncwarp();
   };
+
 
   for (int w = 0; w < (C.ntiles + 31) / 32; ++w) {
     uint32_t m;

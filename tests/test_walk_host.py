@@ -100,3 +100,21 @@ def test_walk_random_histograms(harness):
             N[990:1010] = rng.integers(100, 6000, 20)
         N = N.astype(np.uint32)
         assert _gpu_walk(harness, N) == _oracle(N), trial
+
+
+def test_walk_random_ties(harness):
+    """Few distinct values: flat tops, equal maxima on both sides of a dip,
+    plateaus at minima (ties of the lowest-index maximum and of the leftmost
+    minimum)."""
+    rng = np.random.default_rng(37)
+    levels = np.array([0, 100, 300, 1200, 2500, 4000, 6000, 9000], np.uint32)
+    for trial in range(2000):
+        N = np.zeros(NB, np.uint32)
+        for _ in range(rng.integers(1, 6)):
+            c = int(rng.integers(10, NB - 40))
+            n = int(rng.integers(3, 30))
+            N[c:c + n] = levels[rng.integers(0, len(levels), n)]
+            if rng.random() < 0.5:                   # smooth and quantise: flat tops
+                v = np.convolve(N[c:c + n].astype(float), np.ones(3) / 3, mode="same")
+                N[c:c + n] = (np.round(v / 1500) * 1500).astype(np.uint32)
+        assert _gpu_walk(harness, N) == _oracle(N), trial

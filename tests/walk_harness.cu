@@ -25,9 +25,8 @@ extern "C" int harness_seeds(const uint32_t* N, int nbins, uint32_t thr, uint32_
     const int b = i;
     uint64_t total = 0;
     for (int j = a; j <= b; ++j) total += N[j];
-    pvdev::split_walk(N, a, b, total, C, [&](int l, int h, uint64_t integral) {
-      int im;
-      if (pvdev::keep_piece(N, l, h, integral, C, &im)) {
+    pvdev::split_walk(N, a, b, total, C, [&](int l, int h, uint64_t integral, int im) {
+      if (pvdev::keep_piece(integral, im, C)) {
         if (n < cap) {
           lo[n] = l;
           hi[n] = h;
