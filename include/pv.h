@@ -204,11 +204,11 @@ int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns);
  * real-time loop cannot afford; some applications give all device memory to
  * their own allocator and run with a fixed budget).  Its scratch is a static
  * device array of 8 MiB in the library, held by every GPU that loads the
- * library until the process exits.  A batch of n tracks needs 40 bytes per
+ * library until the process exits.  A batch of n tracks needs 31 bytes per
  * track plus 32 bytes per entry of four vertex work lists (one per size class
  * of at least 1, 9, 17 and 33 tracks) holding min(n / 1, S), min(n / 9, S),
  * min(n / 17, S) and min(n / 33, S) entries, S being the smaller of n and
- * events x out->capacity: about 140,000 tracks of 160-track events at
+ * events x out->capacity: about 165,000 tracks of 160-track events at
  * capacity 64.  Batches needing more are refused with PV_ERR_CAPACITY and a
  * message in pv_last_cuda_error.  The first call on a device looks the array up
  * (cudaGetSymbolAddress); make that first call before any stream capture.
@@ -234,8 +234,8 @@ int pv_launch_config(const pv_ctx* ctx, const pv_tracks* tracks, int* find_threa
                      int* fit_threads, int* find_grid, int* fit_grid);
 
 /* Set the launch shape of an event-size bucket (0: mean tracks per event
- * below 300, 1: below 800, 2: 800 and more) by hand: find kernel 64, 128 or
- * 256 threads, fit kernel 128 or 256.  PV_ERR_ARG for other values. */
+ * below 300, 1: below 800, 2: 800 and more) by hand: find kernel 64, 96, 128
+ * or 256 threads, fit kernel 128 or 256.  PV_ERR_ARG for other values. */
 int pv_set_launch_config(pv_ctx* ctx, int bucket, int find_threads, int fit_threads);
 
 /* Human-readable name of an error code. */

@@ -60,7 +60,7 @@ size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
 // Carves fused-path scratch for a batch out of one buffer.
 struct FusedLayout {
-  size_t counter, center, cid, slot, sorted, A, W, work, total;
+  size_t counter, center, cid, sorted, A, W, work, total;
   int64_t work_cap;
   int64_t cls_cap[pvk::kWorkClasses];
   FusedLayout(int64_t n, int64_t n_events, int cap) {
@@ -73,9 +73,8 @@ struct FusedLayout {
     counter = o; o += 256;
     A = o; o += round16(sizeof(float4) * n);
     W = o; o += round16(sizeof(float2) * n);
-    center = o; o += round16(sizeof(int32_t) * n);
-    cid = o; o += round16(sizeof(int32_t) * n);
-    slot = o; o += round16(sizeof(int32_t) * n);
+    center = o; o += round16(sizeof(int16_t) * n);
+    cid = o; o += round16(sizeof(int8_t) * n);
     sorted = o; o += round16(sizeof(int32_t) * n);
     work = o; o += round16(sizeof(pvk::VertexWork) * work_cap);
     total = o;
@@ -83,9 +82,8 @@ struct FusedLayout {
   pvk::TrackScratch scratch(void* base) const {
     char* b = static_cast<char*>(base);
     pvk::TrackScratch s;
-    s.center = reinterpret_cast<int32_t*>(b + center);
-    s.cid = reinterpret_cast<int32_t*>(b + cid);
-    s.slot = reinterpret_cast<int32_t*>(b + slot);
+    s.center = reinterpret_cast<int16_t*>(b + center);
+    s.cid = reinterpret_cast<int8_t*>(b + cid);
     s.sorted = reinterpret_cast<int32_t*>(b + sorted);
     s.A = reinterpret_cast<float4*>(b + A);
     s.W = reinterpret_cast<float2*>(b + W);
@@ -215,7 +213,7 @@ struct pv_ctx {
   // launch shapes: per event-size bucket, chosen by pv_autotune (default:
   // 128-thread find CTAs, 256-thread fit CTAs, occupancy-sized grids)
   pvk::LaunchCfg bucket_cfg[3];
-  int find_per_sm[4][3] = {};         // [mode][64/128/256]
+  int find_per_sm[4][4] = {};         // [mode][64/96/128/256]
   int fit_per_sm[3][2] = {};          // [accumulation mode][128/256]
   // CUDA graphs of the fused launch, keyed by its arguments
   std::map<std::string, cudaGraphExec_t> graphs;
@@ -362,7 +360,7 @@ pvk::SeedPtrs seed_ptrs(const pv_vertices* s) {
   return S;
 }
 
-int nt_index(int nt) { return nt == 64 ? 0 : (nt == 256 ? 2 : 1); }
+int nt_index(int nt) { return nt == 64 ? 0 : (nt == 96 ? 1 : (nt == 256 ? 3 : 2)); }
 
 int bucket_of(const pv_tracks* t) {
   double mean = t->n_events > 0 ? static_cast<double>(t->n_tracks) / t->n_events : 0.0;
@@ -593,9 +591,9 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
     delete ctx;
     return PV_ERR_CUDA;
   }
-  const int nts[3] = {64, 128, 256};
+  const int nts[4] = {64, 96, 128, 256};
   for (int mode = 1; mode <= 3; ++mode)
-    for (int i = 0; i < 3; ++i) ctx->find_per_sm[mode][i] = pvk::fused_blocks_per_sm(C.nbins, mode, nts[i]);
+    for (int i = 0; i < 4; ++i) ctx->find_per_sm[mode][i] = pvk::fused_blocks_per_sm(C.nbins, mode, nts[i]);
   for (int k = 0; k < 3; ++k)
     for (int i = 0; i < 2; ++i) ctx->fit_per_sm[k][i] = pvk::fit_blocks_per_sm(k, i == 0 ? 128 : 256);
   for (int b = 0; b < 3; ++b) ctx->bucket_cfg[b] = pvk::LaunchCfg{128, 0, pvk::kFitThreads, 0};
@@ -952,7 +950,7 @@ extern "C" int pv_autotune(pv_ctx* ctx, const pv_tracks* sample, pv_vertices* ou
   cudaEvent_t e0, e1;
   PV_CUDA(ctx, cudaEventCreate(&e0));
   PV_CUDA(ctx, cudaEventCreate(&e1));
-  const int finds[3] = {64, 128, 256};
+  const int finds[4] = {64, 96, 128, 256};
   const int fits[2] = {128, 256};
   float best = -1.f;
   pvk::LaunchCfg best_cfg{128, 0, pvk::kFitThreads, 0};

@@ -27,6 +27,10 @@ constexpr float kSMin = 1e-6f;                // narrower profiles fill a single
 constexpr int kGroup = 8;                     // lanes that fit one vertex
 constexpr float kPivotRel = 1e-4f;            // z pivot below this share of M_zz: singular
 constexpr int kGroupsPerWarp = 32 / kGroup;
+// ring of proto-cluster bounds in the peak search: at most 31 are pending
+// when a tile is scanned and a 32-bin tile ends at most 16 runs
+constexpr int kRunRing = 64;
+static_assert(kMaxBins <= 32767, "bin indices are stored as int16");
 
 // Derived settings, passed by value to every kernel.
 struct Consts {
@@ -292,12 +296,12 @@ __device__ __forceinline__ uint32_t bin_or_zero(const uint32_t* N, int j, const 
 
 // Warp-cooperative peak search over a histogram N (shared or global).  If
 // tmask is non-null only tiles (32 bins) whose bit is set can hold non-zero
-// bins; otherwise every tile is scanned.  pc_lo / pc_hi are a 128-entry ring
+// bins; otherwise every tile is scanned.  pc_lo / pc_hi are a kRunRing-entry ring
 // in shared memory.  Writes up to cap seeds into S in z order and returns the
 // number found (which may exceed cap).  All 32 lanes must call it.
 template <bool kSeedZ>
 __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
-                                      SeedOut* S, int cap, int* pc_lo, int* pc_hi) {
+                                      SeedOut* S, int cap, int16_t* pc_lo, int16_t* pc_hi) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int n_seeds = 0;
@@ -324,8 +328,8 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     int a = 0, b = -1;
     uint64_t total = 0;
     if (lane < count) {
-      a = pc_lo[(n_done + lane) & 127];
-      b = pc_hi[(n_done + lane) & 127];
+      a = pc_lo[(n_done + lane) & (kRunRing - 1)];
+      b = pc_hi[(n_done + lane) & (kRunRing - 1)];
       for (int i = a; i <= b; ++i) total += N[i];
     }
     // no piece of a proto-cluster can hold more than its total integral, so
@@ -382,8 +386,10 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
       bool above = v > C.thr;
       unsigned starts = __ballot_sync(0xffffffffu, above && !(vp > C.thr));
       unsigned ends = __ballot_sync(0xffffffffu, above && !(vn > C.thr));
-      if (starts & (1u << lane)) pc_lo[(n_starts + __popc(starts & lt)) & 127] = bin;
-      if (ends & (1u << lane)) pc_hi[(n_ends + __popc(ends & lt)) & 127] = bin;
+      if (starts & (1u << lane))
+        pc_lo[(n_starts + __popc(starts & lt)) & (kRunRing - 1)] = static_cast<int16_t>(bin);
+      if (ends & (1u << lane))
+        pc_hi[(n_ends + __popc(ends & lt)) & (kRunRing - 1)] = static_cast<int16_t>(bin);
       n_starts += __popc(starts);
       n_ends += __popc(ends);
       __syncwarp();

@@ -24,8 +24,7 @@ using namespace pvdev;
 // shared-memory layout of the find kernel
 
 struct Layout {
-  size_t hist, tmask, seeds, pc_lo, pc_hi, alive, part, cnt, voff, base, center, cid, slot, misc,
-      total;
+  size_t hist, tmask, seeds, pc_lo, pc_hi, alive, part, cnt, voff, base, center, cid, misc, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -38,17 +37,16 @@ __host__ __device__ inline Layout make_layout(int nbins, int mode) {
   L.hist = o;   o += find ? sizeof(uint32_t) * ntiles * 32 : 0;
   L.tmask = o;  o += sizeof(uint32_t) * kTileWords;
   L.seeds = o;  o += align_up(sizeof(SeedOut), 16);
-  L.pc_lo = o;  o += sizeof(int) * 128;
-  L.pc_hi = o;  o += sizeof(int) * 128;
+  L.pc_lo = o;  o += sizeof(int16_t) * kRunRing;
+  L.pc_hi = o;  o += sizeof(int16_t) * kRunRing;
   L.alive = o;  o += sizeof(int) * kMaxSeeds;
   L.part = o;   o += sizeof(int) * kMaxSeeds;
   L.cnt = o;    o += sizeof(int) * kMaxSeeds;
   L.voff = o;   o += sizeof(int) * kMaxSeeds;
   L.base = o;   o += sizeof(int) * kMaxSeeds;
-  L.center = o; o += sizeof(int) * kSmallCap;
-  L.cid = o;    o += sizeof(int) * kSmallCap;
-  L.slot = o;   o += sizeof(int) * kSmallCap;
   L.misc = o;   o += sizeof(int) * 8;
+  L.center = o; o += sizeof(int16_t) * kSmallCap;
+  L.cid = o;    o += align_up(sizeof(int8_t) * kSmallCap, 16);
   L.total = align_up(o, 16);
   return L;
 }
@@ -93,6 +91,29 @@ __device__ __forceinline__ void warp_slots(const int* cid, int n, int* base, int
     __syncwarp();
     if (c >= 0) {
       slot[t] = b + rank;
+      if (lane == leader) base[c] = b + __popc(peers);
+    }
+    __syncwarp();
+  }
+}
+
+// The same placement, writing the vertex-ordered list of global track indices
+// (sorted[b0 + position] = b0 + t) instead of per-track slots; warp 0 only.
+template <typename CidT>
+__device__ __forceinline__ void warp_place(const CidT* cid, int n, int* base, int32_t* sorted,
+                                           int64_t b0) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int t0 = 0; t0 < n; t0 += 32) {
+    int t = t0 + lane;
+    int c = t < n ? static_cast<int>(cid[t]) : -1;
+    unsigned peers = __match_any_sync(0xffffffffu, c);
+    int rank = __popc(peers & lt);
+    int leader = __ffs(peers) - 1;
+    int b = c >= 0 ? base[c] : 0;
+    __syncwarp();
+    if (c >= 0) {
+      sorted[b0 + b + rank] = static_cast<int32_t>(b0 + t);
       if (lane == leader) base[c] = b + __popc(peers);
     }
     __syncwarp();
@@ -204,16 +225,15 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem + Lo.hist);
   uint32_t* tmask = reinterpret_cast<uint32_t*>(smem + Lo.tmask);
   SeedOut* S = reinterpret_cast<SeedOut*>(smem + Lo.seeds);
-  int* pc_lo = reinterpret_cast<int*>(smem + Lo.pc_lo);
-  int* pc_hi = reinterpret_cast<int*>(smem + Lo.pc_hi);
+  int16_t* pc_lo = reinterpret_cast<int16_t*>(smem + Lo.pc_lo);
+  int16_t* pc_hi = reinterpret_cast<int16_t*>(smem + Lo.pc_hi);
   int* alive = reinterpret_cast<int*>(smem + Lo.alive);
   int* part = reinterpret_cast<int*>(smem + Lo.part);
   int* cnt = reinterpret_cast<int*>(smem + Lo.cnt);
   int* voff = reinterpret_cast<int*>(smem + Lo.voff);
   int* base = reinterpret_cast<int*>(smem + Lo.base);
-  int* s_center = reinterpret_cast<int*>(smem + Lo.center);
-  int* s_cid = reinterpret_cast<int*>(smem + Lo.cid);
-  int* s_slot = reinterpret_cast<int*>(smem + Lo.slot);
+  int16_t* s_center = reinterpret_cast<int16_t*>(smem + Lo.center);
+  int8_t* s_cid = reinterpret_cast<int8_t*>(smem + Lo.cid);
   int* misc = reinterpret_cast<int*>(smem + Lo.misc);
 
   const int tid = threadIdx.x;
@@ -248,9 +268,8 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
     }
     const int n = static_cast<int>(b1 - b0);
     const bool small = n <= kSmallCap;
-    int* center = small ? s_center : G.center + b0;
-    int* cid = small ? s_cid : G.cid + b0;
-    int* slot = small ? s_slot : G.slot + b0;
+    int16_t* center = small ? s_center : G.center + b0;
+    int8_t* cid = small ? s_cid : G.cid + b0;
     int Ka = 0;
 
     if (MODE & kFind) {
@@ -267,7 +286,7 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
           const int64_t i = b0 + t;
           p = prepare_track(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i], T.cxtx[i],
                             T.ctxtx[i], C);
-          center[t] = p.filled ? p.center : -1;
+          center[t] = static_cast<int16_t>(p.filled ? p.center : -1);
         }
         if (p.filled) {
           int q0 = (p.j0 < 0 ? 0 : p.j0) >> 5;
@@ -331,7 +350,7 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       for (int t = tid; t < n; t += NT) {
         int c = SP.track_vertex[b0 + t];
         c = (c >= 0 && c < K) ? c : -1;
-        cid[t] = c;
+        cid[t] = static_cast<int8_t>(c);
         if (c >= 0) atomicAdd(cnt + c, 1);
         if (O.track_vertex != SP.track_vertex) O.track_vertex[b0 + t] = c;
       }
@@ -347,7 +366,7 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       if (warp == 0) warp_offsets(cnt, Ka, voff, base);
       __syncthreads();
       if (warp == 0) {
-        warp_slots(cid, n, base, slot);
+        warp_place(cid, n, base, G.sorted, b0);
       } else if (warp == 1) {
         // one work item per vertex with tracks, in the list of its size class
         const unsigned lt = (1u << lane) - 1u;
@@ -400,11 +419,6 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
             write_empty_vertex(C, O, S, e, k);
           }
         }
-      }
-      __syncthreads();
-      for (int t = tid; t < n; t += NT) {
-        const int c = cid[t];
-        if (c >= 0) G.sorted[b0 + slot[t]] = static_cast<int32_t>(b0 + t);
       }
     }
     __syncthreads();   // shared state is reused by the next event
@@ -507,11 +521,12 @@ static cudaError_t setup_find_all(int nbins) {
 cudaError_t fused_setup(int nbins) {
   cudaError_t err;
   if ((err = setup_find_all<64>(nbins)) != cudaSuccess) return err;
+  if ((err = setup_find_all<96>(nbins)) != cudaSuccess) return err;
   if ((err = setup_find_all<128>(nbins)) != cudaSuccess) return err;
   return setup_find_all<256>(nbins);
 }
 
-bool find_block_ok(int nt) { return nt == 64 || nt == 128 || nt == 256; }
+bool find_block_ok(int nt) { return nt == 64 || nt == 96 || nt == 128 || nt == 256; }
 bool fit_block_ok(int ft) { return ft == 128 || ft == 256; }
 
 template <int MODE, int NT>
@@ -532,6 +547,7 @@ static int find_blocks_nt(int nbins, int mode) {
 
 int fused_blocks_per_sm(int nbins, int mode, int nt) {
   if (nt == 64) return find_blocks_nt<64>(nbins, mode);
+  if (nt == 96) return find_blocks_nt<96>(nbins, mode);
   if (nt == 256) return find_blocks_nt<256>(nbins, mode);
   return find_blocks_nt<128>(nbins, mode);
 }
@@ -579,6 +595,7 @@ static void launch_find(int nt, int grid, size_t sm, cudaStream_t st, const Cons
                         const TrackPtrs& T, const SeedPtrs& S, const OutPtrs& O,
                         const TrackScratch& ws) {
   if (nt == 64) launch_find_nt<MODE, 64>(grid, sm, st, C, T, S, O, ws);
+  else if (nt == 96) launch_find_nt<MODE, 96>(grid, sm, st, C, T, S, O, ws);
   else if (nt == 256) launch_find_nt<MODE, 256>(grid, sm, st, C, T, S, O, ws);
   else launch_find_nt<MODE, 128>(grid, sm, st, C, T, S, O, ws);
 }
@@ -634,7 +651,7 @@ plain_peaks_kernel(Consts C, TrackPtrs T, const uint32_t* hist, int cap, int32_t
                    int32_t* seed_lo, int32_t* seed_hi, int32_t* seed_bin, float* seed_z,
                    int32_t* ev_status) {
   __shared__ SeedOut S;
-  __shared__ int pc_lo[128], pc_hi[128];
+  __shared__ int16_t pc_lo[kRunRing], pc_hi[kRunRing];
   const int e = blockIdx.x;
   const int64_t b0 = T.off[e], b1 = T.off[e + 1];
   const int lane = threadIdx.x;

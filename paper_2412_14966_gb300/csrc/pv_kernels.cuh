@@ -57,9 +57,8 @@ constexpr int kClassMinTracks[kWorkClasses] = {1, 9, 17, 33};
 
 // Global scratch of the fused path (indexed by the global track index).
 struct TrackScratch {
-  int32_t* center;      // per track, events above kSmallCap tracks
-  int32_t* cid;
-  int32_t* slot;
+  int16_t* center;      // per track, events above kSmallCap tracks: center bin
+  int8_t* cid;          // and vertex index
   int32_t* sorted;      // per track: global track indices in vertex order
   float4* A;            // per track: fit inputs in vertex order
   float2* W;

@@ -37,13 +37,13 @@ def test_every_launch_shape_gives_identical_results():
     tracks = pv.Tracks.from_batch(batch)
     ref = _run(ctx, tracks, pv)
     bucket = 0
-    for fi in (64, 128, 256):
+    for fi in (64, 96, 128, 256):
         for ft in (128, 256):
             ctx.set_launch_config(bucket, fi, ft)
             assert ctx.launch_config(tracks)[:2] == (fi, ft)
             _same(_run(ctx, tracks, pv), ref, batch)
     with pytest.raises(pv.PVError):
-        ctx.set_launch_config(bucket, 96, 256)
+        ctx.set_launch_config(bucket, 100, 256)
     ctx.close()
 
 
@@ -74,10 +74,10 @@ def test_autotuner_sets_the_bucket_of_its_sample():
     ts, tp = pv.Tracks.from_batch(small), pv.Tracks.from_batch(pileup)
     ref_s, ref_p = _run(ctx, ts, pv), _run(ctx, tp, pv)
     cfg_p = ctx.autotune(tp)
-    assert cfg_p[0] in (64, 128, 256) and cfg_p[1] in (128, 256)
+    assert cfg_p[0] in (64, 96, 128, 256) and cfg_p[1] in (128, 256)
     assert ctx.launch_config(ts)[:2] == (128, 256)        # bucket 0 untouched
     cfg_s = ctx.autotune(ts)
-    assert cfg_s[0] in (64, 128, 256) and cfg_s[1] in (128, 256)
+    assert cfg_s[0] in (64, 96, 128, 256) and cfg_s[1] in (128, 256)
     _same(_run(ctx, ts, pv), ref_s, small)
     _same(_run(ctx, tp, pv), ref_p, pileup)
     ctx.close()
