@@ -27,6 +27,7 @@ _LIB = None
 ONE = 4096  # histogram weight of one track (reading R3 in pv_oracle.c)
 
 CONVERGED, MAXITER, SINGULAR, REJ_BEAM, REJ_NTRK, ACCEPTED = 1, 2, 4, 8, 16, 32
+DUPLICATE = 64   # multi-vertex fit: rejected as a duplicate (reading R15)
 EV_SEED_OVERFLOW = 1
 
 TRACK_FIELDS = ("x", "y", "z", "tx", "ty", "cxx", "cxtx", "ctxtx", "cyy", "cyty", "ctyty")
@@ -48,6 +49,25 @@ class Params(C.Structure):
         ("max_seeds", C.c_int32),
         ("x_b", C.c_float), ("y_b", C.c_float), ("tx_b", C.c_float), ("ty_b", C.c_float),
     ]
+
+
+class MvParams(C.Structure):
+    """Settings of the GPU-flavour multi-vertex fit (readings R12-R15)."""
+    _fields_ = [("chi2_cut", C.c_double), ("dz_tol", C.c_double), ("w_assoc", C.c_double),
+                ("dup_sep2", C.c_double), ("max_iter", C.c_int32)]
+
+
+def default_mv_params(**kw) -> MvParams:
+    m = MvParams(
+        chi2_cut=4.0,        # Sec. 3.5, weight figure: chi2_max = 4 (R12)
+        dz_tol=0.5e-3,       # Sec. 3.5: GPU rule |dz| < 0.5 um (R13)
+        w_assoc=0.5,         # R14: the weight of a track at chi2 = chi2_cut alone
+        dup_sep2=25.0,       # Sec. 3.5: dz^2 / (sum of z variances) below 25 (R15)
+        max_iter=10,         # Sec. 3.5: at most ten iterations
+    )
+    for k, v in kw.items():
+        setattr(m, k, v)
+    return m
 
 
 def default_params(**kw) -> Params:
@@ -123,6 +143,8 @@ def lib():
         L.oc_seeds_from_hist.restype = C.c_int
         L.oc_associate_bins.argtypes = [ip, C.c_int64, ip, ip, ip, C.c_int, pp, ip, ip]
         L.oc_associate_bins.restype = C.c_int
+        L.oc_mv_fit_batch.argtypes = [arr11, i64p, C.c_int32, pp, P(MvParams), fp, fp, fp, ip,
+                                      dp, dp, dp, dp, dp, dp, ip, ip, ip, ip]
         _LIB = L
     return _LIB
 
@@ -260,6 +282,36 @@ def fit_batch(batch, found: dict, p: Params) -> dict:
                        _ptr(out["ndof"], C.c_double), _ptr(out["n_tracks"], C.c_int32),
                        _ptr(out["n_iter"], C.c_int32), _ptr(out["status"], C.c_int32))
     out["n"] = ns.copy()
+    return out
+
+
+def mv_fit_batch(batch, found: dict, p: Params, m: MvParams | None = None) -> dict:
+    """GPU-flavour multi-vertex fit of every seed (Sec. 3.5, readings R12-R15),
+    duplicate removal and final selection.  ``found`` holds the seeds (x, y, z,
+    n) as find_batch returns them.  Adds ``track_vertex`` (R14)."""
+    m = m or default_mv_params()
+    arr, keep = _tracks_arg(batch.tracks)
+    E = batch.n_events
+    cap = p.max_seeds
+    offs = np.ascontiguousarray(batch.offsets, dtype=np.int64)
+    out = {k: np.zeros((E, cap), np.float64) for k in ("x", "y", "z", "chi2", "ndof")}
+    out["cov"] = np.zeros((E, cap, 6), np.float64)
+    out.update({k: np.zeros((E, cap), np.int32) for k in ("n_tracks", "n_iter", "status")})
+    tv = np.full(max(batch.n_tracks, 1), -1, np.int32)
+    sx = np.ascontiguousarray(found["x"], np.float32)
+    sy = np.ascontiguousarray(found["y"], np.float32)
+    sz = np.ascontiguousarray(found["z"], np.float32)
+    ns = np.ascontiguousarray(found["n"], np.int32)
+    lib().oc_mv_fit_batch(arr, _ptr(offs, C.c_int64), E, C.byref(p), C.byref(m),
+                          _ptr(sx, C.c_float), _ptr(sy, C.c_float), _ptr(sz, C.c_float),
+                          _ptr(ns, C.c_int32), _ptr(out["x"], C.c_double),
+                          _ptr(out["y"], C.c_double), _ptr(out["z"], C.c_double),
+                          _ptr(out["cov"], C.c_double), _ptr(out["chi2"], C.c_double),
+                          _ptr(out["ndof"], C.c_double), _ptr(out["n_tracks"], C.c_int32),
+                          _ptr(out["n_iter"], C.c_int32), _ptr(out["status"], C.c_int32),
+                          _ptr(tv, C.c_int32))
+    out["n"] = ns.copy()
+    out["track_vertex"] = tv[:batch.n_tracks]
     return out
 
 

@@ -694,3 +694,228 @@ int oc_associate_bins(const int32_t* center, int64_t n, const int32_t* lo, const
   free(s);
   return r;
 }
+
+/* ========================================================================= */
+/* GPU-flavour multi-vertex fit (Sec. 3.5, implicit track association)      */
+/*
+ * Readings:
+ *   R12 weights (Sec. 3.5, Eq. of w_ij): w_ij = exp(-chi2_ij / 2) /
+ *       (exp(-chi2_cut / 2) + sum_k exp(-chi2_ik / 2)), k over every seed of
+ *       the event.  For a competing vertex k != j, chi2_ik is taken at k's seed
+ *       position (the paper keeps the other vertices at their initial
+ *       positions, so the fits are independent); for k = j at j's current
+ *       position.  W_ik is V^-1 extrapolated to seed k's z (R2); a track that is
+ *       not usable for seed k (R10) adds nothing to that term.  chi2_cut = 4,
+ *       the value of the paper's weight figure.
+ *   R13 the fit stops when |dz| < 0.5 um (no dchi2 condition, Sec. 3.5 GPU
+ *       rule), at most max_iter iterations; singular matrices as R11.
+ *   R14 a vertex's tracks are those with w_ij >= 0.5 in its last iteration; a
+ *       track belongs to the vertex with its largest last-iteration weight when
+ *       that weight is >= 0.5 (lowest index on ties), otherwise to none.
+ *   R15 duplicates: in seed (z) order every non-singular vertex is compared with
+ *       the last one kept; if dz^2 < dup_sep2 (C_zz + C_zz') the one with fewer
+ *       tracks is rejected (the earlier one when equal).  The final selection of
+ *       Sec. 3.5 then applies to the rest.
+ */
+typedef struct {
+  double chi2_cut;      /* 4 */
+  double dz_tol;        /* 0.5e-3 mm */
+  double w_assoc;       /* 0.5 */
+  double dup_sep2;      /* 25 */
+  int32_t max_iter;     /* 10 */
+} oc_mv_params;
+
+#define OC_DUPLICATE 64
+
+/* chi2 of a track (fit inputs for some seed) at the point (x, y, z), Eq. chi2 */
+static double oc_mv_chi2(const oc_fit_track* f, double x, double y, double z) {
+  double rx = f->x + (z - f->z) * f->tx - x;
+  double ry = f->y + (z - f->z) * f->ty - y;
+  return rx * rx * f->wx + ry * ry * f->wy;
+}
+
+/* R12 with comp = sum over the competing seeds of exp(-chi2_ik / 2) */
+static double oc_mv_weight(double c2, double comp, const oc_mv_params* m) {
+  double e = exp(-0.5 * c2);
+  return e / (exp(-0.5 * m->chi2_cut) + comp + e);
+}
+
+/* Fit of one vertex with the multi-vertex weights (same normal equations as
+ * oc_fit_vertex, R7).  a_prev receives the position the last weights were
+ * taken at. */
+static void oc_mv_fit_vertex(const oc_fit_track* trk, const double* comp, int n, double xs,
+                             double ys, double zs, const oc_mv_params* m, oc_vertex* out,
+                             double a_prev[3]) {
+  double alpha[3] = {xs, ys, zs};
+  double Minv[3][3] = {{0}};
+  double chi2_last = 0.0, dchi2_last = 0.0, sw_last = 0.0;
+  int nw_last = 0, status = 0, it_done = 0;
+  a_prev[0] = xs; a_prev[1] = ys; a_prev[2] = zs;
+  for (int it = 1; it <= m->max_iter; ++it) {
+    double M[3][3] = {{0}}, g[3] = {0, 0, 0};
+    double chi2 = 0.0, sw = 0.0;
+    int nw = 0;
+    for (int a = 0; a < 3; ++a) a_prev[a] = alpha[a];
+    for (int i = 0; i < n; ++i) {
+      if (!trk[i].usable) continue;
+      double r[2];
+      r[0] = trk[i].x + (alpha[2] - trk[i].z) * trk[i].tx - alpha[0];
+      r[1] = trk[i].y + (alpha[2] - trk[i].z) * trk[i].ty - alpha[1];
+      double W[2] = {trk[i].wx, trk[i].wy};
+      double c2 = r[0] * r[0] * W[0] + r[1] * r[1] * W[1];
+      double w = oc_mv_weight(c2, comp[i], m);
+      double H[2][3] = {{-1.0, 0.0, trk[i].tx}, {0.0, -1.0, trk[i].ty}};
+      for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+          double s = 0.0;
+          for (int c = 0; c < 2; ++c) s += H[c][a] * W[c] * H[c][b];
+          M[a][b] += w * s;
+        }
+        double s = 0.0;
+        for (int c = 0; c < 2; ++c) s += H[c][a] * W[c] * r[c];
+        g[a] += w * s;
+      }
+      chi2 += w * c2;
+      sw += w;
+      if (w >= m->w_assoc) nw++;
+    }
+    it_done = it;
+    if (!oc_inverse3(M, Minv)) {
+      status = OC_SINGULAR;
+      chi2_last = chi2; sw_last = sw; nw_last = nw; dchi2_last = 0.0;
+      break;
+    }
+    double step[3];
+    for (int a = 0; a < 3; ++a) {
+      step[a] = 0.0;
+      for (int b = 0; b < 3; ++b) step[a] -= Minv[a][b] * g[b];
+    }
+    double dchi2 = 0.0;
+    for (int a = 0; a < 3; ++a) dchi2 += g[a] * step[a];
+    for (int a = 0; a < 3; ++a) alpha[a] += step[a];
+    chi2_last = chi2; dchi2_last = dchi2; sw_last = sw; nw_last = nw;
+    if (fabs(step[2]) < m->dz_tol) {                 /* R13 */
+      status = OC_CONVERGED;
+      break;
+    }
+    if (it == m->max_iter) status = OC_MAXITER;
+  }
+  if (m->max_iter <= 0) status = OC_MAXITER;
+  out->x = alpha[0];
+  out->y = alpha[1];
+  out->z = alpha[2];
+  out->cov[0] = Minv[0][0];
+  out->cov[1] = Minv[0][1];
+  out->cov[2] = Minv[1][1];
+  out->cov[3] = Minv[0][2];
+  out->cov[4] = Minv[1][2];
+  out->cov[5] = Minv[2][2];
+  out->chi2 = chi2_last + dchi2_last;
+  out->ndof = 2.0 * sw_last - 3.0;
+  out->n_tracks = nw_last;
+  out->n_iter = it_done;
+  out->status = status;
+}
+
+/* Multi-vertex fit of every seed of every event (seeds as oc_find_batch writes
+ * them, rows of p->max_seeds), duplicate removal and final selection.
+ * track_vertex: per track, R14. */
+int oc_mv_fit_batch(const float* const* T, const int64_t* offsets, int32_t n_events,
+                    const oc_params* p, const oc_mv_params* m, const float* seed_x,
+                    const float* seed_y, const float* seed_z, const int32_t* n_seeds,
+                    double* vx, double* vy, double* vz, double* vcov, double* vchi2,
+                    double* vndof, int32_t* vntrk, int32_t* vniter, int32_t* vstatus,
+                    int32_t* track_vertex) {
+  int cap = p->max_seeds;
+  for (int32_t e = 0; e < n_events; ++e) {
+    int64_t b = offsets[e], n = offsets[e + 1] - b;
+    int K = n_seeds[e];
+    size_t nn = (size_t)(n > 0 ? n : 1), kk = (size_t)(K > 0 ? K : 1);
+    double* E = (double*)malloc(sizeof(double) * nn * kk);     /* exp(-chi2_ik/2) at seed k */
+    oc_fit_track* ft = (oc_fit_track*)malloc(sizeof(oc_fit_track) * nn);
+    double* comp = (double*)malloc(sizeof(double) * nn);
+    double* prev = (double*)malloc(sizeof(double) * 3 * kk);
+    for (int k = 0; k < K; ++k) {
+      size_t o = (size_t)e * cap + k;
+      for (int64_t i = 0; i < n; ++i) {
+        oc_fit_track f;
+        oc_fit_track_from(T, b + i, seed_z[o], &f);
+        E[i * kk + k] = f.usable ? exp(-0.5 * oc_mv_chi2(&f, seed_x[o], seed_y[o], seed_z[o]))
+                                 : 0.0;
+      }
+    }
+    for (int j = 0; j < K; ++j) {
+      size_t o = (size_t)e * cap + j;
+      for (int64_t i = 0; i < n; ++i) {
+        oc_fit_track_from(T, b + i, seed_z[o], &ft[i]);
+        double c = 0.0;
+        for (int k = 0; k < K; ++k)
+          if (k != j) c += E[i * kk + k];
+        comp[i] = c;
+      }
+      oc_vertex v;
+      oc_mv_fit_vertex(ft, comp, (int)n, seed_x[o], seed_y[o], seed_z[o], m, &v, prev + 3 * j);
+      vx[o] = v.x; vy[o] = v.y; vz[o] = v.z;
+      for (int c = 0; c < 6; ++c) vcov[o * 6 + c] = v.cov[c];
+      vchi2[o] = v.chi2; vndof[o] = v.ndof;
+      vntrk[o] = v.n_tracks; vniter[o] = v.n_iter; vstatus[o] = v.status;
+    }
+    /* R14: each track's vertex from the last-iteration weights */
+    for (int64_t i = 0; i < n; ++i) {
+      int best = -1;
+      double wbest = -1.0;
+      for (int j = 0; j < K; ++j) {
+        size_t o = (size_t)e * cap + j;
+        if (vstatus[o] & OC_SINGULAR) continue;
+        oc_fit_track f;
+        oc_fit_track_from(T, b + i, seed_z[o], &f);
+        if (!f.usable) continue;
+        double c = 0.0;
+        for (int k = 0; k < K; ++k)
+          if (k != j) c += E[i * kk + k];
+        double w = oc_mv_weight(oc_mv_chi2(&f, prev[3 * j], prev[3 * j + 1], prev[3 * j + 2]),
+                                c, m);
+        if (w > wbest) { wbest = w; best = j; }
+      }
+      track_vertex[b + i] = (best >= 0 && wbest >= m->w_assoc) ? best : -1;
+    }
+    /* R15: duplicates, then the final selection (Sec. 3.5, Table smog-pp) */
+    int last = -1;
+    for (int j = 0; j < K; ++j) {
+      size_t o = (size_t)e * cap + j;
+      if (vstatus[o] & OC_SINGULAR) continue;
+      if (last >= 0) {
+        size_t ol = (size_t)e * cap + last;
+        double dz = vz[o] - vz[ol];
+        if (dz * dz < m->dup_sep2 * (vcov[o * 6 + 5] + vcov[ol * 6 + 5])) {
+          if (vntrk[o] > vntrk[ol]) {
+            vstatus[ol] |= OC_DUPLICATE;
+            last = j;
+          } else {
+            vstatus[o] |= OC_DUPLICATE;
+          }
+          continue;
+        }
+      }
+      last = j;
+    }
+    for (int j = 0; j < K; ++j) {
+      size_t o = (size_t)e * cap + j;
+      int st = vstatus[o];
+      if (st & (OC_SINGULAR | OC_DUPLICATE)) continue;
+      int gas = vz[o] < (double)p->z_gas;
+      if (!gas) {
+        double bx = (double)p->x_b + (double)p->tx_b * vz[o];
+        double by = (double)p->y_b + (double)p->ty_b * vz[o];
+        double r = sqrt((vx[o] - bx) * (vx[o] - bx) + (vy[o] - by) * (vy[o] - by));
+        if (r > p->max_r_beam) st |= OC_REJ_BEAM;
+      }
+      int need = gas ? p->min_pv_tracks_gas : p->min_pv_tracks_pp;
+      if (vntrk[o] < need) st |= OC_REJ_NTRK;
+      if (!(st & (OC_REJ_BEAM | OC_REJ_NTRK))) st |= OC_ACCEPTED;
+      vstatus[o] = st;
+    }
+    free(E); free(ft); free(comp); free(prev);
+  }
+  return 0;
+}
