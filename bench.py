@@ -447,6 +447,22 @@ def run_ours(args):
     plain_ms = ps.elapsed_time(pe) / plain_steps
     plain.close()
 
+    # the GPU flavour of the fit (multi-vertex, Sec. 3.5): find + multi-vertex
+    # fit kernels on the same batch, same timing
+    mouts = [pv.Vertices.empty(E, NT) for _ in range(2)]
+    for i in range(max(args.warmup, 1)):
+        ctx.fit_multi(reps[i % N_REPLICAS], out=mouts[i % 2], stream=stream)
+    torch.cuda.synchronize()
+    multi_steps = max(1, min(args.steps, 200))
+    ms_, me_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms_.record(stream)
+    for i in range(multi_steps):
+        ctx.fit_multi(reps[i % N_REPLICAS], out=mouts[i % 2], stream=stream)
+    me_.record(stream)
+    torch.cuda.synchronize()
+    multi_ms = ms_.elapsed_time(me_) / multi_steps
+    del mouts
+
     # end to end through the C ABI with host buffers (pinned), copies included
     host = pv.Tracks.from_host(batch, pinned=True)
     hout = pv.Vertices.empty(E, NT, host=True, pinned=True, bins=False)
@@ -486,6 +502,9 @@ def run_ours(args):
                      "kernel": "fused step: find_kernel<3> + fit_kernel<0> (one launch each)"},
         "plain": {"value": E * world / (plain_ms / 1e3), "ms_per_step": plain_ms,
                   "path": "one kernel per step, global-memory histograms"},
+        "multi": {"value": E * world / (multi_ms / 1e3), "ms_per_step": multi_ms,
+                  "path": "find kernel + multi-vertex fit kernel (pv_fit_multi, GPU flavour "
+                          "of the fit: implicit association, duplicate removal)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "pv_run_host (pinned host buffers)"},
         "clocks": clk,

@@ -47,6 +47,7 @@ extern "C" {
 #define PV_ST_REJ_BEAM 8    /* pp vertex farther than max_r_beam from the beamline */
 #define PV_ST_REJ_NTRK 16   /* fewer than min_pv_tracks tracks with weight > 0 */
 #define PV_ST_ACCEPTED 32   /* a primary vertex of the final selection (Sec. 3.5) */
+#define PV_ST_DUPLICATE 64  /* multi-vertex fit: rejected as a duplicate of a nearby vertex */
 
 /* ---- event status bits -------------------------------------------------- */
 #define PV_EV_SEED_OVERFLOW 1  /* more seed clusters than the capacity; extra ones dropped */
@@ -92,6 +93,11 @@ typedef struct {
   int32_t reserved;                 /* 0 */
   uint64_t pool_bytes;              /* serving: device bytes admitted requests may pin (0 = 1 GiB) */
   uint64_t max_spin_ns;             /* serving: bound of every wait (0 = 10 s) */
+  /* multi-vertex fit (pv_fit_multi, Sec. 3.5 GPU implementation) */
+  float mv_chi2_cut;                /* chi2_max of the multi-vertex weight (weight figure): 4 */
+  float mv_dz_tol;                  /* convergence |dz| (Sec. 3.5, GPU rule): 0.0005 mm */
+  float mv_w_assoc;                 /* weight from which a track counts for a vertex: 0.5 */
+  float mv_dup_sep2;                /* duplicates: dz^2 < mv_dup_sep2 (C_zz + C_zz') (Sec. 3.5): 25 */
 } pv_config;
 
 /* Tracks in structure-of-arrays layout (Sec. 5, x86: one contiguous array per
@@ -156,6 +162,24 @@ int pv_find_batch(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* seeds_out, 
  * seeds == NULL runs find and fit as one fused pass (the fast path).
  * Asynchronous on cuda_stream. */
 int pv_fit_batch(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
+                 pv_vertices* out, void* cuda_stream);
+
+/* The GPU flavour of step (d) (Sec. 3.5): every seed of an event is fitted
+ * with weights that share each track among all vertices,
+ * w_ij = exp(-chi2_ij/2) / (exp(-mv_chi2_cut/2) + sum_k exp(-chi2_ik/2)),
+ * the other vertices k entering at their seed positions; iterations stop at
+ * |dz| < mv_dz_tol (at most max_iter).  Then vertices closer than
+ * dz^2 < mv_dup_sep2 (C_zz + C_zz') to the last kept one (seed order) lose
+ * to the one with more tracks (PV_ST_DUPLICATE), and the final selection of
+ * Sec. 3.5 applies.  A vertex's tracks (n_tracks, the track minimum) are those
+ * with w >= mv_w_assoc in its last iteration; out->track_vertex receives each
+ * track's vertex of largest last-iteration weight if that weight is
+ * >= mv_w_assoc, else -1.  Every usable track of an event enters every fit.
+ * seeds (device): positions and n_per_event as pv_find_batch writes them, or
+ * NULL to find the seeds first (into out).  out (device) as for
+ * pv_fit_batch.  Binary32 per-track terms and sums.  Asynchronous on
+ * cuda_stream. */
+int pv_fit_multi(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
                  pv_vertices* out, void* cuda_stream);
 
 /* Step (a) alone: z_poca, sigma_poca and the center bin (-1 = not filled) of

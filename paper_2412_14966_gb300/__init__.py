@@ -22,6 +22,7 @@ TRACK_FIELDS = ("x", "y", "z", "tx", "ty", "cxx", "cxtx", "ctxtx", "cyy", "cyty"
 PV_OK, PV_ERR_ARG, PV_ERR_CUDA, PV_ERR_CAPACITY, PV_ERR_NOMEM = 0, 1, 2, 3, 4
 PV_ERR_TIMEOUT, PV_ERR_BUSY, PV_ERR_NOTFOUND = 5, 6, 7
 ST_CONVERGED, ST_MAXITER, ST_SINGULAR, ST_REJ_BEAM, ST_REJ_NTRK, ST_ACCEPTED = 1, 2, 4, 8, 16, 32
+ST_DUPLICATE = 64
 EV_SEED_OVERFLOW, EV_BAD_OFFSETS = 1, 4
 ONE = 4096
 MAX_SEEDS = 64
@@ -33,6 +34,7 @@ EXPORTED = (
     "pv_extrapolate_batch", "pv_histogram_batch", "pv_num_bins", "pv_run_host", "pv_submit",
     "pv_poll", "pv_request_latency_ns", "pv_strerror", "pv_last_cuda_error", "pv_launch_count",
     "pv_find_fit_static", "pv_autotune", "pv_launch_config", "pv_set_launch_config",
+    "pv_fit_multi",
 )
 
 
@@ -62,6 +64,8 @@ class pv_config(C.Structure):
         ("accum_mode", C.c_int32), ("path", C.c_int32),
         ("use_graph", C.c_int32), ("reserved", C.c_int32),
         ("pool_bytes", C.c_uint64), ("max_spin_ns", C.c_uint64),
+        ("mv_chi2_cut", C.c_float), ("mv_dz_tol", C.c_float), ("mv_w_assoc", C.c_float),
+        ("mv_dup_sep2", C.c_float),
     ]
 
 
@@ -105,6 +109,8 @@ def load():
     L.pv_destroy.argtypes = [C.c_void_p]
     L.pv_find_batch.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
     L.pv_fit_batch.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), P(pv_vertices),
+                               C.c_void_p]
+    L.pv_fit_multi.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), P(pv_vertices),
                                C.c_void_p]
     L.pv_extrapolate_batch.argtypes = [C.c_void_p, P(pv_tracks), C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]
@@ -296,6 +302,17 @@ class Context:
         s = seeds.struct() if seeds is not None else None
         self._check(self.lib.pv_fit_batch(self.h, C.byref(t), C.byref(s) if s is not None else None,
                                           C.byref(o), _stream_handle(stream)), "pv_fit_batch")
+        return out
+
+    def fit_multi(self, tracks: Tracks, seeds: Vertices | None = None, out: Vertices | None = None,
+                  stream=None) -> Vertices:
+        """``pv_fit_multi``: the multi-vertex fit of every seed (seeds = None:
+        find them first)."""
+        out = out or Vertices.empty(tracks.n_events, tracks.n_tracks)
+        t, o = tracks.struct(), out.struct()
+        s = seeds.struct() if seeds is not None else None
+        self._check(self.lib.pv_fit_multi(self.h, C.byref(t), C.byref(s) if s is not None else None,
+                                          C.byref(o), _stream_handle(stream)), "pv_fit_multi")
         return out
 
     def extrapolate_batch(self, tracks: Tracks, stream=None):

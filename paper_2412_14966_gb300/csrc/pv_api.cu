@@ -218,7 +218,8 @@ struct pv_ctx {
   // CUDA graphs of the fused launch, keyed by its arguments
   std::map<std::string, cudaGraphExec_t> graphs;
   cudaStream_t capture_stream = nullptr;
-  DevBuf fused_ws, plain_ws;
+  DevBuf fused_ws, plain_ws, mv_ws;
+  int mv_per_sm = 0;
   // host-buffer entry point staging
   DevBuf host_in, host_out;
   cudaStream_t own_stream = nullptr;
@@ -262,6 +263,9 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
     return PV_ERR_ARG;
   if (cfg.path != PV_PATH_FUSED && cfg.path != PV_PATH_PLAIN) return PV_ERR_ARG;
   if (!(cfg.min_integral_pp >= 0.0f) || !(cfg.min_integral_gas >= 0.0f)) return PV_ERR_ARG;
+  if (!(cfg.mv_chi2_cut > 0.0f) || !(cfg.mv_dz_tol >= 0.0f) || !(cfg.mv_w_assoc > 0.0f) ||
+      !(cfg.mv_w_assoc <= 1.0f) || !(cfg.mv_dup_sep2 >= 0.0f))
+    return PV_ERR_ARG;
   C->z_min = cfg.z_min;
   C->dz = cfg.dz;
   {
@@ -281,6 +285,10 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
   C->dchi2_tol = cfg.dchi2_tol;
   C->dz_tol = cfg.dz_tol;
   C->max_r_beam = cfg.max_r_beam;
+  C->mv_ecut = static_cast<float>(std::exp(-0.5 * static_cast<double>(cfg.mv_chi2_cut)));
+  C->mv_dz_tol = cfg.mv_dz_tol;
+  C->mv_w_assoc = cfg.mv_w_assoc;
+  C->mv_dup_sep2 = cfg.mv_dup_sep2;
   C->thr = cfg.bin_threshold;
   C->t_pp = static_cast<uint32_t>(std::llround(static_cast<double>(cfg.min_integral_pp) * PV_ONE));
   C->t_gas = static_cast<uint32_t>(std::llround(static_cast<double>(cfg.min_integral_gas) * PV_ONE));
@@ -565,6 +573,10 @@ void pv_config_default(pv_config* c) {
   c->reserved = 0;
   c->pool_bytes = 0;
   c->max_spin_ns = 0;
+  c->mv_chi2_cut = 4.0f;
+  c->mv_dz_tol = 0.0005f;
+  c->mv_w_assoc = 0.5f;
+  c->mv_dup_sep2 = 25.0f;
 }
 
 int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** out) {
@@ -597,6 +609,7 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
   for (int k = 0; k < 3; ++k)
     for (int i = 0; i < 2; ++i) ctx->fit_per_sm[k][i] = pvk::fit_blocks_per_sm(k, i == 0 ? 128 : 256);
   for (int b = 0; b < 3; ++b) ctx->bucket_cfg[b] = pvk::LaunchCfg{128, 0, pvk::kFitThreads, 0};
+  ctx->mv_per_sm = pvk::mv_blocks_per_sm();
   *out = ctx;
   return PV_OK;
 }
@@ -631,6 +644,7 @@ int pv_destroy(pv_ctx* ctx) {
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   ctx->fused_ws.release();
   ctx->plain_ws.release();
+  ctx->mv_ws.release();
   ctx->host_in.release();
   ctx->host_out.release();
   ctx->pool.release();
@@ -666,6 +680,65 @@ int pv_fit_batch(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
   cudaSetDevice(ctx->device);
   return run_find_or_fit(ctx, tracks, seeds, out, static_cast<cudaStream_t>(stream),
                          seeds ? pvk::kFit : pvk::kFindFit);
+}
+
+int pv_fit_multi(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds, pv_vertices* out,
+                 void* stream) {
+  if (!ctx) return PV_ERR_ARG;
+  int rc = check_tracks(tracks);
+  if (rc != PV_OK) return rc;
+  rc = check_out(out, tracks, true);
+  if (rc != PV_OK) return rc;
+  if (seeds) {
+    rc = check_out(seeds, tracks, true);
+    if (rc != PV_OK) return rc;
+  }
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (tracks->n_events == 0) return PV_OK;
+  if (!seeds) {
+    // the seeds of steps (a)-(c), written into out and read back per event
+    rc = run_find_or_fit(ctx, tracks, nullptr, out, st, pvk::kFind);
+    if (rc != PV_OK) return rc;
+    seeds = out;
+  }
+  // scratch of the three multi-vertex kernels
+  const int64_t E = tracks->n_events, n = tracks->n_tracks;
+  const int64_t slots = E * PV_MAX_SEEDS;
+  size_t o = 0;
+  const size_t o_cnt = o; o += 256;
+  const size_t o_K = o; o += round16(sizeof(int) * E);
+  const size_t o_S = o; o += round16(sizeof(float) * n);
+  const size_t o_work = o; o += round16(sizeof(int2) * slots);
+  const size_t o_sx = o; o += round16(sizeof(float) * slots);
+  const size_t o_sy = o; o += round16(sizeof(float) * slots);
+  const size_t o_sz = o; o += round16(sizeof(float) * slots);
+  const size_t o_last = o; o += round16(sizeof(pvk::MvLastState) * slots);
+  const size_t o_vz = o; o += round16(sizeof(float) * slots);
+  const size_t o_vczz = o; o += round16(sizeof(float) * slots);
+  const size_t o_vn = o; o += round16(sizeof(int) * slots);
+  const size_t o_vst = o; o += round16(sizeof(int) * slots);
+  PV_CUDA(ctx, ctx->mv_ws.ensure(o));
+  char* base = static_cast<char*>(ctx->mv_ws.p);
+  pvk::MvScratch M;
+  M.counters = reinterpret_cast<int*>(base + o_cnt);
+  M.K = reinterpret_cast<int*>(base + o_K);
+  M.S = reinterpret_cast<float*>(base + o_S);
+  M.work = reinterpret_cast<int2*>(base + o_work);
+  M.sx = reinterpret_cast<float*>(base + o_sx);
+  M.sy = reinterpret_cast<float*>(base + o_sy);
+  M.sz = reinterpret_cast<float*>(base + o_sz);
+  M.last = reinterpret_cast<pvk::MvLastState*>(base + o_last);
+  M.vz = reinterpret_cast<float*>(base + o_vz);
+  M.vczz = reinterpret_cast<float*>(base + o_vczz);
+  M.vn = reinterpret_cast<int*>(base + o_vn);
+  M.vst = reinterpret_cast<int*>(base + o_vst);
+  const int fit_grid = ctx->n_sm * (ctx->mv_per_sm > 0 ? ctx->mv_per_sm : 1);
+  int launches = 0;
+  PV_CUDA(ctx, pvk::launch_mv_fit(ctx->C, track_ptrs(tracks), seed_ptrs(seeds), out_ptrs(out), M,
+                                  fit_grid, st, &launches));
+  ctx->launches += launches;
+  return PV_OK;
 }
 
 int pv_extrapolate_batch(pv_ctx* ctx, const pv_tracks* tracks, float* zpoca, float* sigma,

@@ -46,6 +46,9 @@ struct Consts {
   int32_t nbins, ntiles, gas_bin;
   int32_t max_iter;
   int32_t accum_mode;
+  // multi-vertex fit
+  float mv_ecut;            // exp(-chi2_cut / 2)
+  float mv_dz_tol, mv_w_assoc, mv_dup_sep2;
 };
 
 // ---------------------------------------------------------------------------

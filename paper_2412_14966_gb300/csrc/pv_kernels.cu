@@ -498,6 +498,369 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
 }
 
 // ---------------------------------------------------------------------------
+// GPU-flavour multi-vertex fit (Sec. 3.5): every track enters every vertex of
+// its event with w_ij = exp(-chi2_ij/2) / (exp(-chi2_cut/2) + sum_k
+// exp(-chi2_ik/2)), the other vertices k at their seed positions.
+
+// A track's fit inputs for one vertex and its competing term: the sum over the
+// event's seeds of exp(-chi2/2) at the seed positions (S) without this
+// vertex's own seed term.
+struct MvTrack {
+  float X, Y, tx, ty, wx, wy, comp;
+};
+
+__device__ __forceinline__ float mv_seed_term(float X, float Y, float wx, float wy) {
+  return __expf(-0.5f * (X * X * wx + Y * Y * wy));
+}
+
+__device__ __forceinline__ bool mv_track(const TrackPtrs& T, int64_t t, float xs, float ys,
+                                         float zs, float S, MvTrack* m) {
+  float4 A;
+  float2 W;
+  make_fit_track(T.x[t], T.y[t], T.z[t], T.tx[t], T.ty[t], T.cxx[t], T.cxtx[t], T.ctxtx[t],
+                 T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, &A, &W);
+  if (!(W.x > 0.0f)) return false;
+  m->X = A.x; m->Y = A.y; m->tx = A.z; m->ty = A.w; m->wx = W.x; m->wy = W.y;
+  const float c = S - mv_seed_term(A.x, A.y, W.x, W.y);
+  m->comp = c > 0.0f ? c : 0.0f;
+  return true;
+}
+
+__device__ __forceinline__ float mv_weight(float c2, float comp, const Consts& C) {
+  const float e = __expf(-0.5f * c2);
+  return e / (C.mv_ecut + comp + e);
+}
+
+// The sheared position (and shear) a vertex's last weights were taken at.
+using MvLast = MvLastState;
+
+__device__ __forceinline__ float mv_chi2_at(const MvTrack& m, const MvLast& L) {
+  const float dtx = m.tx - L.cx, dty = m.ty - L.cy;
+  const float rx = m.X + L.az * dtx - L.axp;
+  const float ry = m.Y + L.az * dty - L.ayp;
+  return rx * rx * m.wx + ry * ry * m.wy;
+}
+
+// Multi-vertex fit of one vertex per 8-lane group (binary32 sums).  visit(f)
+// calls f(const MvTrack&) for each of this lane's tracks of the vertex (lane
+// r of the group takes every 8th).  Same normal equations, shear and solve as
+// group_fit; the stop rule is |dz| < mv_dz_tol alone and a track counts for
+// the vertex from weight mv_w_assoc on.  Every lane of the warp must call it.
+template <class Visit>
+__device__ void group_fit_multi(Visit&& visit, bool active, const Consts& C, VertexOut* out,
+                                MvLast* last) {
+  float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+  if (active)
+    visit([&](const MvTrack& m) {
+      m0 += m.wx; m1 += m.wx * m.tx; m2 += m.wy; m3 += m.wy * m.ty;
+    });
+  m0 = group_sum(m0); m1 = group_sum(m1); m2 = group_sum(m2); m3 = group_sum(m3);
+  float cx = m0 > 0.f ? m1 / m0 : 0.f;
+  float cy = m2 > 0.f ? m3 / m2 : 0.f;
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  bool done = !active;
+  int status = 0, n_iter = 0, nw = 0;
+  float c2sum = 0.f, sw = 0.f, dchi2 = 0.f;
+  float ix = 0.f, iy = 0.f, ux = 0.f, uy = 0.f, is = 0.f;
+  MvLast L{0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int it = 1; it <= C.max_iter; ++it) {
+    float v[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) v[q] = 0.f;
+    int cnt_w = 0;
+    const MvLast P{ax - cx * az, ay - cy * az, az, cx, cy};
+    if (!done)
+      visit([&](const MvTrack& m) {
+        const float dtx = m.tx - P.cx, dty = m.ty - P.cy;
+        const float rx = m.X + P.az * dtx - P.axp;
+        const float ry = m.Y + P.az * dty - P.ayp;
+        const float c2 = rx * rx * m.wx + ry * ry * m.wy;
+        const float w = mv_weight(c2, m.comp, C);
+        const float wx = w * m.wx, wy = w * m.wy;
+        v[0] += wx; v[1] += wy;
+        v[2] += wx * dtx; v[3] += wy * dty;
+        v[4] += wx * dtx * dtx + wy * dty * dty;
+        v[5] += wx * rx; v[6] += wy * ry;
+        v[7] += wx * dtx * rx + wy * dty * ry;
+        v[8] += w * c2; v[9] += w;
+        if (w >= C.mv_w_assoc) ++cnt_w;
+      });
+#pragma unroll
+    for (int q = 0; q < 10; ++q) v[q] = group_sum(v[q]);
+    cnt_w = group_sum_i(cnt_w);
+    if (!done) {
+      const float sxx = v[0], syy = v[1], sxz = v[2], syz = v[3], szz = v[4];
+      const float bx = v[5], by = v[6], bz = v[7];
+      n_iter = it;
+      c2sum = v[8]; sw = v[9]; nw = cnt_w;
+      L = P;
+      float s_ = 0.f;
+      bool ok = sxx > 0.f && syy > 0.f && isfinite(sxx) && isfinite(syy);
+      if (ok) {
+        ix = 1.0f / sxx;
+        iy = 1.0f / syy;
+        ux = sxz * ix;
+        uy = syz * iy;
+        s_ = szz - sxz * ux - syz * uy;
+        const float mzz = szz + 2.0f * (cx * sxz + cy * syz) + cx * cx * sxx + cy * cy * syy;
+        ok = s_ > kPivotRel * mzz && isfinite(s_);
+      }
+      if (!ok) {
+        status = PV_ST_SINGULAR;
+        dchi2 = 0.f;
+        done = true;
+      } else {
+        is = 1.0f / s_;
+        const float dz = (ux * bx + uy * by - bz) * is;
+        const float dx = (bx + sxz * dz) * ix;
+        const float dy = (by + syz * dz) * iy;
+        dchi2 = -bx * dx - by * dy + bz * dz;
+        ax += dx + cx * dz;
+        ay += dy + cy * dz;
+        az += dz;
+        ux += cx;
+        uy += cy;
+        cx = ux;
+        cy = uy;
+        if ((dz < 0.f ? -dz : dz) < C.mv_dz_tol) {
+          status = PV_ST_CONVERGED;
+          done = true;
+        } else if (it == C.max_iter) {
+          status = PV_ST_MAXITER;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+  if (!active) return;
+  *last = L;
+  out->x = ax;
+  out->y = ay;
+  out->z = az;
+  out->cov[0] = ix + ux * ux * is;
+  out->cov[1] = ux * uy * is;
+  out->cov[2] = iy + uy * uy * is;
+  out->cov[3] = ux * is;
+  out->cov[4] = uy * is;
+  out->cov[5] = is;
+  out->chi2 = c2sum + dchi2;
+  out->ndof = 2.0f * sw - 3.0f;
+  out->n_tracks = nw;
+  out->n_iter = n_iter;
+  out->status = status == 0 ? PV_ST_MAXITER : status;
+}
+
+// The multi-vertex fit runs as three kernels:
+//   mv_seed_kernel   one warp per event: each track's seed sum S (global) and
+//                    one work item (event, vertex) per seed;
+//   mv_fit_kernel    persistent, four vertices per warp from the work list,
+//                    any event: the fits (group_fit_multi);
+//   mv_final_kernel  one warp per event: each track's vertex from the last-
+//                    iteration weights, duplicates in seed order, selection.
+
+__global__ void __launch_bounds__(kMvThreads)
+mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
+  const int lane = threadIdx.x & 31;
+  const int e = (blockIdx.x * kMvThreads + threadIdx.x) >> 5;
+  if (e >= T.n_events) return;                       // whole warps
+  const int64_t b0 = T.off[e], b1 = T.off[e + 1];
+  if (offsets_bad(b0, b1, T.n_tracks)) {
+    if (lane == 0) {
+      O.n_per_event[e] = 0;
+      if (O.event_status) O.event_status[e] = PV_EV_BAD_OFFSETS;
+      M.K[e] = 0;
+    }
+    return;
+  }
+  const int n = static_cast<int>(b1 - b0);
+  int capk = SP.cap < O.cap ? SP.cap : O.cap;
+  capk = capk < kMaxSeeds ? capk : kMaxSeeds;
+  int K = SP.n_per_event[e];
+  K = K < 0 ? 0 : (K > capk ? capk : K);
+  // seeds of this event in registers: lane k holds seeds k and k + 32
+  float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, sx1 = 0.f, sy1 = 0.f, sz1 = 0.f;
+  if (lane < K) {
+    const size_t q = static_cast<size_t>(e) * SP.cap + lane;
+    sx0 = SP.x[q]; sy0 = SP.y[q]; sz0 = SP.z[q];
+  }
+  if (lane + 32 < K) {
+    const size_t q = static_cast<size_t>(e) * SP.cap + lane + 32;
+    sx1 = SP.x[q]; sy1 = SP.y[q]; sz1 = SP.z[q];
+  }
+  // the seeds are copied to the per-slot scratch (the output rows may be the
+  // seed rows and are overwritten by the fits)
+  if (lane < K) {
+    const size_t q = static_cast<size_t>(e) * kMaxSeeds + lane;
+    M.sx[q] = sx0; M.sy[q] = sy0; M.sz[q] = sz0;
+  }
+  if (lane + 32 < K) {
+    const size_t q = static_cast<size_t>(e) * kMaxSeeds + lane + 32;
+    M.sx[q] = sx1; M.sy[q] = sy1; M.sz[q] = sz1;
+  }
+  for (int t0 = 0; t0 < n; t0 += 32) {        // warp-uniform: the loop shuffles
+    const int t = t0 + lane;
+    const bool valid = t < n;
+    const int64_t i = b0 + (valid ? t : 0);
+    const float x = T.x[i], y = T.y[i], z = T.z[i], tx = T.tx[i], ty = T.ty[i];
+    const float a = T.cxx[i], b = T.cxtx[i], c = T.ctxtx[i];
+    const float d = T.cyy[i], f = T.cyty[i], g = T.ctyty[i];
+    float sum = 0.f;
+    for (int k = 0; k < K; ++k) {
+      const int src = k & 31;
+      const float kx = __shfl_sync(0xffffffffu, k < 32 ? sx0 : sx1, src);
+      const float ky = __shfl_sync(0xffffffffu, k < 32 ? sy0 : sy1, src);
+      const float kz = __shfl_sync(0xffffffffu, k < 32 ? sz0 : sz1, src);
+      float4 A;
+      float2 W;
+      make_fit_track(x, y, z, tx, ty, a, b, c, d, f, g, kx, ky, kz, &A, &W);
+      if (W.x > 0.0f) sum += mv_seed_term(A.x, A.y, W.x, W.y);
+    }
+    if (valid) M.S[i] = sum;
+  }
+  // work items: one per seed
+  int wb = 0;
+  if (lane == 0) {
+    M.K[e] = K;
+    O.n_per_event[e] = K;
+    wb = K > 0 ? atomicAdd(M.counters, K) : 0;
+  }
+  wb = __shfl_sync(0xffffffffu, wb, 0);
+  for (int k = lane; k < K; k += 32) M.work[wb + k] = make_int2(e, k);
+}
+
+// Multi-vertex fits from the work list: every 8-lane group fits one vertex,
+// its lanes visiting every track of the event.
+__global__ void __launch_bounds__(kMvFitThreads)
+mv_fit_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
+  const int lane = threadIdx.x & 31;
+  const int r = lane & (kGroup - 1);
+  const int n_items = M.counters[0];
+  for (;;) {
+    int b = 0;
+    if (lane == 0) b = atomicAdd(M.counters + 1, kGroupsPerWarp);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (b >= n_items) break;
+    const int v = b + (lane >> 3);
+    const bool has = v < n_items;
+    const int2 it = has ? M.work[v] : make_int2(0, 0);
+    const int e = it.x, k = it.y;
+    const int64_t b0 = has ? T.off[e] : 0;
+    const int n = has ? static_cast<int>(T.off[e + 1] - b0) : 0;
+    const size_t slot = static_cast<size_t>(e) * kMaxSeeds + k;
+    const float xs = has ? M.sx[slot] : 0.f, ys = has ? M.sy[slot] : 0.f;
+    const float zs = has ? M.sz[slot] : 0.f;
+    const float* S = M.S + b0;
+    auto every = [&](auto&& f) {
+      for (int s = r; s < n; s += kGroup) {
+        MvTrack m;
+        if (mv_track(T, b0 + s, xs, ys, zs, S[s], &m)) f(m);
+      }
+    };
+    VertexOut out;
+    MvLast L;
+    group_fit_multi(every, has, C, &out, &L);
+    if (has && r == 0) {
+      const size_t q = static_cast<size_t>(e) * O.cap + k;
+      O.x[q] = xs + out.x;
+      O.y[q] = ys + out.y;
+      O.z[q] = zs + out.z;
+      if (O.cov) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) O.cov[q * 6 + c] = out.cov[c];
+      }
+      if (O.chi2) O.chi2[q] = out.chi2;
+      if (O.ndof) O.ndof[q] = out.ndof;
+      if (O.n_tracks) O.n_tracks[q] = out.n_tracks;
+      if (O.n_iter) O.n_iter[q] = out.n_iter;
+      M.last[slot] = L;
+      M.vz[slot] = zs + out.z;
+      M.vczz[slot] = out.cov[5];
+      M.vn[slot] = out.n_tracks;
+      M.vst[slot] = out.status;
+    }
+  }
+}
+
+// Each track's vertex, then duplicates and the final selection; one warp per
+// event.
+__global__ void __launch_bounds__(kMvThreads)
+mv_final_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
+  const int lane = threadIdx.x & 31;
+  const int e = (blockIdx.x * kMvThreads + threadIdx.x) >> 5;
+  if (e >= T.n_events) return;
+  const int K = M.K[e];
+  const int64_t b0 = T.off[e], b1 = T.off[e + 1];
+  if (offsets_bad(b0, b1, T.n_tracks)) return;
+  const int n = static_cast<int>(b1 - b0);
+  const size_t s0 = static_cast<size_t>(e) * kMaxSeeds;
+  for (int t = lane; t < n; t += 32) {
+    int best = -1;
+    float wbest = -1.0f;
+    for (int j = 0; j < K; ++j) {
+      if (M.vst[s0 + j] & PV_ST_SINGULAR) continue;
+      MvTrack m;
+      if (!mv_track(T, b0 + t, M.sx[s0 + j], M.sy[s0 + j], M.sz[s0 + j], M.S[b0 + t], &m))
+        continue;
+      const float w = mv_weight(mv_chi2_at(m, M.last[s0 + j]), m.comp, C);
+      if (w > wbest) {
+        wbest = w;
+        best = j;
+      }
+    }
+    O.track_vertex[b0 + t] = (best >= 0 && wbest >= C.mv_w_assoc) ? best : -1;
+  }
+  if (lane == 0) {
+    int kept = -1;
+    for (int j = 0; j < K; ++j) {
+      int st = M.vst[s0 + j];
+      if (st & PV_ST_SINGULAR) continue;
+      if (kept >= 0) {
+        const float dz = M.vz[s0 + j] - M.vz[s0 + kept];
+        if (dz * dz < C.mv_dup_sep2 * (M.vczz[s0 + j] + M.vczz[s0 + kept])) {
+          if (M.vn[s0 + j] > M.vn[s0 + kept]) {
+            M.vst[s0 + kept] |= PV_ST_DUPLICATE;
+            kept = j;
+          } else {
+            M.vst[s0 + j] |= PV_ST_DUPLICATE;
+          }
+          continue;
+        }
+      }
+      kept = j;
+    }
+    for (int j = 0; j < K; ++j) {
+      const size_t q = static_cast<size_t>(e) * O.cap + j;
+      int st = M.vst[s0 + j];
+      if (!(st & (PV_ST_SINGULAR | PV_ST_DUPLICATE)))
+        st = select_vertex(O.x[q], O.y[q], M.vz[s0 + j], M.vn[s0 + j], st, C);
+      if (O.status) O.status[q] = st;
+    }
+  }
+}
+
+cudaError_t launch_mv_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
+                          const OutPtrs& O, const MvScratch& M, int fit_grid, cudaStream_t st,
+                          int* n_launches) {
+  cudaError_t err = cudaMemsetAsync(M.counters, 0, 2 * sizeof(int), st);
+  if (err != cudaSuccess) return err;
+  const int per_block = kMvThreads / 32;
+  const int grid = (T.n_events + per_block - 1) / per_block;
+  mv_seed_kernel<<<grid, kMvThreads, 0, st>>>(C, T, S, O, M);
+  mv_fit_kernel<<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
+  mv_final_kernel<<<grid, kMvThreads, 0, st>>>(C, T, O, M);
+  *n_launches += 3;
+  return cudaGetLastError();
+}
+
+int mv_blocks_per_sm(void) {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mv_fit_kernel, kMvFitThreads, 0) !=
+      cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+// ---------------------------------------------------------------------------
 // launch plumbing: kernel instantiations by block size
 
 template <int MODE, int NT>

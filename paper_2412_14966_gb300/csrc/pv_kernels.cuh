@@ -148,6 +148,27 @@ inline long long class_capacity(int c, long long n_tracks, long long n_events, i
 int fused_blocks_per_sm(int nbins, int mode);
 int fit_blocks_per_sm(bool kahan);
 
+// Multi-vertex fit (GPU flavour of Sec. 3.5) of the seeds S into O.
+struct MvLastState {        // the sheared position a vertex's last weights were taken at
+  float axp, ayp, az, cx, cy;
+};
+struct MvScratch {
+  int* counters;            // [0] work items listed, [1] next item to fit
+  int* K;                   // per event: seeds fitted
+  float* S;                 // per track: sum over the event's seeds of exp(-chi2/2)
+  int2* work;               // (event, seed) per vertex
+  float *sx, *sy, *sz;      // per slot [event][kMaxSeeds]: seed position
+  MvLastState* last;        // per slot: last-iteration state
+  float *vz, *vczz;         // per slot: fitted z and C_zz
+  int *vn, *vst;            // per slot: tracks and status
+};
+constexpr int kMvThreads = 128;        // per-event kernels: one warp per event
+constexpr int kMvFitThreads = 256;
+cudaError_t launch_mv_fit(const pvdev::Consts& C, const TrackPtrs& T, const SeedPtrs& S,
+                          const OutPtrs& O, const MvScratch& M, int fit_grid, cudaStream_t st,
+                          int* n_launches);
+int mv_blocks_per_sm(void);
+
 cudaError_t launch_plain_find(const pvdev::Consts& C, const TrackPtrs& T, const OutPtrs& O,
                               const PlainScratch& ws, cudaStream_t st, int* n_launches);
 cudaError_t launch_plain_fit(const pvdev::Consts& C, const TrackPtrs& T, const SeedPtrs& S,

@@ -164,3 +164,36 @@ def assert_fit_close(gpu, ref, n_seeds, tight_pair=None, cond=None):
             assert abs(gt["z"][e, k] - rt["z"][e, k]) < TOL_Z, (e, k)
             assert cov_error(gt["cov"][e, k], rt["cov"][e, k]) < TOL_COV, (e, k)
     return worst, len(differ)
+
+
+def _ulp_moved(t: dict, rng) -> dict:
+    out = {}
+    for kk, v in t.items():
+        v = np.asarray(v, np.float32)
+        up = rng.integers(0, 2, v.shape).astype(bool)
+        out[kk] = np.where(up, np.nextafter(v, np.float32(np.inf)),
+                           np.nextafter(v, np.float32(-np.inf))).astype(np.float32)
+    return out
+
+
+def mv_spread(batch, found: dict, p, e: int, k: int, n_draw: int = 8):
+    """The multi-vertex analogue of cov_spread: the largest change of the
+    oracle's fitted x/y, z (mm) and covariance of vertex (e, k) over n_draw
+    refits of event e whose binary32 track inputs are each moved by one ulp
+    (the seeds stay).  Returns (xy, z, cov)."""
+    from paper_2412_14966_gb300 import synthetic
+    b0, b1 = int(batch.offsets[e]), int(batch.offsets[e + 1])
+    t = {kk: vv[b0:b1] for kk, vv in batch.tracks.items()}
+    seeds = {kk: found[kk][e:e + 1] for kk in ("x", "y", "z")}
+    seeds["n"] = found["n"][e:e + 1]
+    base = oracle.mv_fit_batch(synthetic.batch_from_events([t]), seeds, p)
+    rng = np.random.default_rng(1000 * e + k)
+    wxy = wz = wc = 0.0
+    for _ in range(n_draw):
+        r = oracle.mv_fit_batch(synthetic.batch_from_events([_ulp_moved(t, rng)]), seeds, p)
+        if r["status"][0, k] & oracle.SINGULAR:
+            continue
+        wxy = max(wxy, abs(r["x"][0, k] - base["x"][0, k]), abs(r["y"][0, k] - base["y"][0, k]))
+        wz = max(wz, abs(r["z"][0, k] - base["z"][0, k]))
+        wc = max(wc, cov_error(r["cov"][0, k], base["cov"][0, k]))
+    return wxy, wz, wc

@@ -55,7 +55,8 @@ int main(void) {
   printf("{\n");
   F(pv_config, z_min); F(pv_config, bin_threshold); F(pv_config, chi2_max);
   F(pv_config, max_iter); F(pv_config, accum_mode); F(pv_config, path);
-  F(pv_config, pool_bytes); F(pv_config, max_spin_ns);
+  F(pv_config, pool_bytes); F(pv_config, max_spin_ns); F(pv_config, mv_chi2_cut);
+  F(pv_config, mv_dup_sep2);
   F(pv_tracks, x); F(pv_tracks, ctyty); F(pv_tracks, event_offsets);
   F(pv_tracks, n_tracks); F(pv_tracks, n_events);
   F(pv_vertices, x); F(pv_vertices, cov); F(pv_vertices, bin_max);
@@ -114,6 +115,12 @@ def test_default_config_is_the_papers(lib):
     assert abs(c.dz_tol - g["converge_dz_mm"]["value"]) < 1e-9
     assert c.max_iter == g["max_iterations"]["value"]
     assert abs(c.max_r_beam - g["max_beamline_distance_mm"]["value"]) < 1e-7
+    assert c.mv_chi2_cut == g["multivertex_chi2_max"]["value"]
+    assert abs(c.mv_dz_tol - g["gpu_converge_dz_mm"]["value"]) < 1e-9
+    assert c.mv_dup_sep2 == g["duplicate_separation"]["value"]
+    m = oracle.default_mv_params()
+    assert (m.chi2_cut, m.dup_sep2, m.w_assoc) == (c.mv_chi2_cut, c.mv_dup_sep2, c.mv_w_assoc)
+    assert abs(m.dz_tol - c.mv_dz_tol) < 1e-9
     # the unstated settings agree between library and oracle
     p = oracle.default_params()
     assert (c.bin_threshold, c.dip_num, c.dip_den) == (p.bin_threshold, p.dip_num, p.dip_den)
