@@ -541,19 +541,23 @@ __device__ __forceinline__ float mv_chi2_at(const MvTrack& m, const MvLast& L) {
   return rx * rx * m.wx + ry * ry * m.wy;
 }
 
-// Multi-vertex fit of one vertex per 8-lane group (binary32 sums).  visit(f)
-// calls f(const MvTrack&) for each of this lane's tracks of the vertex (lane
-// r of the group takes every 8th).  Same normal equations, shear and solve as
-// group_fit; the stop rule is |dz| < mv_dz_tol alone and a track counts for
-// the vertex from weight mv_w_assoc on.  Every lane of the warp must call it.
-template <class Visit>
-__device__ void group_fit_multi(Visit&& visit, bool active, const Consts& C, VertexOut* out,
-                                MvLast* last) {
+// Multi-vertex fit of one vertex per 8-lane group (binary32 sums), over all n
+// tracks of the event starting at global index b0 (lane r of the group takes
+// every 8th); S[s] is track s's seed sum.  Same normal equations, shear and
+// solve as group_fit; the stop rule is |dz| < mv_dz_tol alone and a track
+// counts for the vertex from weight mv_w_assoc on.  Every lane of the warp
+// must call it.
+__device__ void group_fit_multi(const TrackPtrs& T, int64_t b0, int n, const float* S,
+                                float xs, float ys, float zs, bool active, const Consts& C,
+                                VertexOut* out, MvLast* last) {
+  const int r = threadIdx.x & (kGroup - 1);
+  const int cnt = active ? n : 0;
   float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-  if (active)
-    visit([&](const MvTrack& m) {
-      m0 += m.wx; m1 += m.wx * m.tx; m2 += m.wy; m3 += m.wy * m.ty;
-    });
+  for (int s = r; s < cnt; s += kGroup) {
+    MvTrack m;
+    if (!mv_track(T, b0 + s, xs, ys, zs, S[s], &m)) continue;
+    m0 += m.wx; m1 += m.wx * m.tx; m2 += m.wy; m3 += m.wy * m.ty;
+  }
   m0 = group_sum(m0); m1 = group_sum(m1); m2 = group_sum(m2); m3 = group_sum(m3);
   float cx = m0 > 0.f ? m1 / m0 : 0.f;
   float cy = m2 > 0.f ? m3 / m2 : 0.f;
@@ -569,8 +573,10 @@ __device__ void group_fit_multi(Visit&& visit, bool active, const Consts& C, Ver
     for (int q = 0; q < 10; ++q) v[q] = 0.f;
     int cnt_w = 0;
     const MvLast P{ax - cx * az, ay - cy * az, az, cx, cy};
-    if (!done)
-      visit([&](const MvTrack& m) {
+    if (!done) {
+      for (int s = r; s < cnt; s += kGroup) {
+        MvTrack m;
+        if (!mv_track(T, b0 + s, xs, ys, zs, S[s], &m)) continue;
         const float dtx = m.tx - P.cx, dty = m.ty - P.cy;
         const float rx = m.X + P.az * dtx - P.axp;
         const float ry = m.Y + P.az * dty - P.ayp;
@@ -584,7 +590,8 @@ __device__ void group_fit_multi(Visit&& visit, bool active, const Consts& C, Ver
         v[7] += wx * dtx * rx + wy * dty * ry;
         v[8] += w * c2; v[9] += w;
         if (w >= C.mv_w_assoc) ++cnt_w;
-      });
+      }
+    }
 #pragma unroll
     for (int q = 0; q < 10; ++q) v[q] = group_sum(v[q]);
     cnt_w = group_sum_i(cnt_w);
@@ -749,16 +756,9 @@ mv_fit_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
     const size_t slot = static_cast<size_t>(e) * kMaxSeeds + k;
     const float xs = has ? M.sx[slot] : 0.f, ys = has ? M.sy[slot] : 0.f;
     const float zs = has ? M.sz[slot] : 0.f;
-    const float* S = M.S + b0;
-    auto every = [&](auto&& f) {
-      for (int s = r; s < n; s += kGroup) {
-        MvTrack m;
-        if (mv_track(T, b0 + s, xs, ys, zs, S[s], &m)) f(m);
-      }
-    };
     VertexOut out;
     MvLast L;
-    group_fit_multi(every, has, C, &out, &L);
+    group_fit_multi(T, b0, n, M.S + b0, xs, ys, zs, has, C, &out, &L);
     if (has && r == 0) {
       const size_t q = static_cast<size_t>(e) * O.cap + k;
       O.x[q] = xs + out.x;

@@ -128,6 +128,8 @@ def generate(
     fake_frac: float = 0.1,
     pv_z_sigma: float = 45.0,
     pv_xy_sigma: float = 0.015,
+    gas_overlay: bool = False,
+    beam=(0.0, 0.0, 0.0, 0.0),
     name: str = "",
 ) -> EventBatch:
     """Draw ``n_events`` independent events.
@@ -138,6 +140,9 @@ def generate(
     z ~ U(-541, -341) mm and slopes uniform on the disk |t| < 0.15.
     ``secondary_frac`` of the PVs are displaced by an exponential flight of mean
     1 mm along a random direction with a positive z component.
+    ``gas_overlay`` adds one p-gas PV to every event (pp + p-gas overlay).
+    ``beam`` = (x_b, y_b, t_x,b, t_y,b): PVs are placed around the beamline
+    x_b + t_x,b z, y_b + t_y,b z (the beamline at z = 0 and its slopes).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     if isinstance(mu, tuple):
@@ -146,9 +151,15 @@ def generate(
         mu_ev = np.full(n_events, float(mu))
     n_pv = np.maximum(rng.poisson(mu_ev), 1).astype(np.int64)
     gas_ev = rng.uniform(size=n_events) < gas_event_frac
+    if gas_overlay:
+        n_pv = n_pv + 1                    # the last PV of each event is the p-gas one
     total_pv = int(n_pv.sum())
     pv_event = np.repeat(np.arange(n_events, dtype=np.int64), n_pv)
     pv_gas = gas_ev[pv_event]
+    if gas_overlay:
+        last = np.cumsum(n_pv) - 1
+        pv_gas = pv_gas.copy()
+        pv_gas[last] = True
 
     pv_z = rng.normal(0.0, pv_z_sigma, size=total_pv)
     pv_z_gas = rng.uniform(-541.0, -341.0, size=total_pv)
@@ -165,6 +176,9 @@ def generate(
     pv_x = pv_x + d * sin_t * np.cos(phi)
     pv_y = pv_y + d * sin_t * np.sin(phi)
     pv_z = pv_z + d * cos_t
+    if any(beam):
+        pv_x = pv_x + beam[0] + beam[2] * pv_z
+        pv_y = pv_y + beam[1] + beam[3] * pv_z
 
     p_nb = 2.0 / (2.0 + mean_tracks)
     ntrk = 1 + rng.negative_binomial(2, p_nb, size=total_pv).astype(np.int64)
@@ -263,11 +277,23 @@ def workload_pileup(n_events: int = 20_000, seed: int = 3) -> EventBatch:
     return generate(n_events, seed, mu=40.0, mean_tracks=28.0, name="pp-mu40-m28")
 
 
+def workload_overlay(n_events: int = 2000, seed: int = 5, beam=(0.0, 0.0, 0.0, 0.0)) -> EventBatch:
+    """pp events (mu = 5) each overlaid with one p-gas PV in the gas cell
+    (Sec. 4, the pp + p-gas overlay sample), around the given beamline."""
+    return generate(n_events, seed, mu=5.0, mean_tracks=28.0, gas_overlay=True, beam=beam,
+                    name="pp-mu5-plus-gas")
+
+
+# a beamline displaced and inclined like a crossing angle (unit: mm, rad)
+TILTED_BEAM = (0.6, -0.35, 2.0e-4, -1.5e-4)
+
+
 WORKLOADS = {
     "small": workload_small,
     "nominal": workload_nominal,
     "mixture": workload_mixture,
     "pileup": workload_pileup,
+    "overlay": workload_overlay,
 }
 
 

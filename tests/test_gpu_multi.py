@@ -43,21 +43,21 @@ def _gpu(pv, batch, **cfg):
     return out
 
 
-def _tight_pair(pv, batch, ref):
+def _tight_pair(pv, batch, ref, p=None, beam=(0.0, 0.0, 0.0, 0.0)):
     """Both sides refitted from the same seeds for 1000 iterations with no
     stopping rule (the paper's rule looks at dz alone, so x and y may still
     move when it fires).  Also returns where the oracle has settled: its
     results after 999 and 1000 iterations agree to a hundredth of the
     tolerances."""
     import torch
-    ctx = pv.Context(device=0, mv_dz_tol=0.0, max_iter=1000)
+    ctx = pv.Context(device=0, beamline=beam, mv_dz_tol=0.0, max_iter=1000)
     t = pv.Tracks.from_batch(batch)
     seeds = ctx.find_batch(t)
     v = ctx.fit_multi(t, seeds=seeds)
     torch.cuda.synchronize()
     g = v.numpy()
     ctx.close()
-    p = oracle.default_params()
+    p = p or oracle.default_params()
     r = oracle.mv_fit_batch(batch, ref, p, oracle.default_mv_params(dz_tol=0.0, max_iter=1000))
     r0 = oracle.mv_fit_batch(batch, ref, p, oracle.default_mv_params(dz_tol=0.0, max_iter=999))
     settled = ((np.abs(r["x"] - r0["x"]) < G.TOL_XY / 100) & (np.abs(r["y"] - r0["y"]) < G.TOL_XY / 100)
@@ -65,7 +65,9 @@ def _tight_pair(pv, batch, ref):
     return g, r, settled
 
 
-def _compare(pv, batch, g, ref, fit):
+def _compare(pv, batch, g, ref, fit, p=None):
+    p = p or oracle.default_params()
+    beam = (p.x_b, p.y_b, p.tx_b, p.ty_b)
     E = batch.n_events
     assert np.array_equal(g["n_per_event"][:E], ref["n"])
     K = fit["z"].shape[1]
@@ -95,7 +97,7 @@ def _compare(pv, batch, g, ref, fit):
                 assert np.isfinite(gg["z"][e, k]) and np.isfinite(gg["cov"][e, k]).all()
                 special.append(("degenerate", where, int(e), int(k)))
                 continue
-            sxy, sz, sc = G.mv_spread(bat, fnd, oracle.default_params(), e, k)
+            sxy, sz, sc = G.mv_spread(bat, fnd, p, e, k)
             for err, tol, spr in ((dxy[e, k], G.TOL_XY, sxy), (dz[e, k], G.TOL_Z, sz),
                                   (ce, G.TOL_COV, sc)):
                 assert err < tol or (spr >= tol / F and err < F * spr), (where, e, k, err, tol, spr)
@@ -112,8 +114,8 @@ def _compare(pv, batch, g, ref, fit):
     events = np.nonzero(rest.any(axis=1))[0]
     if len(events):
         sub = batch.subset(events)
-        sref = oracle.find_batch(sub, oracle.default_params())
-        gt, rt, settled = _tight_pair(pv, sub, sref)
+        sref = oracle.find_batch(sub, p)
+        gt, rt, settled = _tight_pair(pv, sub, sref, p, beam)
         srest = rest[events]
         fixed = srest & settled & ((rt["status"] & oracle.SINGULAR) == 0)
         # candidates that do not settle (limit cycles) are rare
@@ -192,3 +194,16 @@ def test_multi_vertex_edge_cases(pv):
     fit = oracle.mv_fit_batch(batch, ref, p)
     _compare(pv, batch, g, ref, fit)
     assert g["n_per_event"][0] == 0 and g["n_per_event"][1] == 0
+
+
+@pytest.mark.parametrize("tilted", [False, True])
+def test_multi_vertex_fit_on_the_overlay(pv, tilted):
+    """pp + one p-gas PV per event, straight and inclined beamline."""
+    beam = synthetic.TILTED_BEAM if tilted else (0.0, 0.0, 0.0, 0.0)
+    batch = synthetic.workload_overlay(n_events=600, seed=9, beam=beam)
+    g = _gpu(pv, batch, beamline=beam)
+    p = G.oracle_params_for(beam=beam)
+    ref = oracle.find_batch(batch, p)
+    fit = oracle.mv_fit_batch(batch, ref, p)
+    rep = _compare(pv, batch, g, ref, fit, p)
+    print("overlay", tilted, rep)

@@ -258,3 +258,24 @@ def test_run_host_equals_device_path(ctx, pv, small):
         for k in ("x", "y", "z", "cov", "status", "n_iter"):
             assert np.array_equal(o[k][e, :n], v[k][e, :n]), (k, e)
     assert np.array_equal(o["track_vertex"][:small.n_tracks], v["track_vertex"][:small.n_tracks])
+
+
+@pytest.mark.parametrize("tilted", [False, True])
+def test_pp_plus_gas_overlay(pv, tilted):
+    """pp events each overlaid with one p-gas PV (the paper's pp + p-gas
+    sample), around a straight or a displaced and inclined beamline (Eq.
+    zpocadef with beam slopes, reading R1): every event against the oracle."""
+    beam = synthetic.TILTED_BEAM if tilted else (0.0, 0.0, 0.0, 0.0)
+    batch = synthetic.workload_overlay(n_events=1000, seed=7, beam=beam)
+    ctx = pv.Context(device=0, beamline=beam)
+    s, v = G.gpu_find_fit(ctx, batch)
+    ctx.close()
+    p = G.oracle_params_for(beam=beam)
+    ref = oracle.find_batch(batch, p)
+    G.assert_find_equal(s, ref, batch)
+    # both regions produce seeds
+    zs = ref["z"][np.arange(64)[None, :] < ref["n"][:, None]]
+    assert (zs < -300).sum() > 0.8 * batch.n_events and (zs > -300).sum() > batch.n_events
+    fit = oracle.fit_batch(batch, ref, p)
+    G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref, beam=beam),
+                       cond=(batch, ref, p))
