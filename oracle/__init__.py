@@ -48,6 +48,7 @@ class Params(C.Structure):
         ("max_r_beam", C.c_double),
         ("max_seeds", C.c_int32),
         ("x_b", C.c_float), ("y_b", C.c_float), ("tx_b", C.c_float), ("ty_b", C.c_float),
+        ("split_mode", C.c_int32),
     ]
 
 
@@ -86,6 +87,7 @@ def default_params(**kw) -> Params:
         max_r_beam=0.3,                              # Sec. 3.5: 0.3 mm from the beamline
         max_seeds=64,
         x_b=0.0, y_b=0.0, tx_b=0.0, ty_b=0.0,
+        split_mode=0,                                # Sec. 3.3: GPU (z order); 1 = x86 (R16)
     )
     for k, v in kw.items():
         setattr(p, k, v)

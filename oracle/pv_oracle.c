@@ -38,6 +38,9 @@
  *      above OC_PIVOT_REL times its diagonal element (for example a single
  *      weighted track, or tracks that are all parallel): the vertex gets the
  *      SINGULAR status instead of a step along an undetermined direction.
+ *   R16 the x86 dip splitting (split_mode 1): the smallest bin between the two
+ *      largest maxima, with the significance and integral tests of R5, applied
+ *      recursively to both sides (see oc_split_recursive).
  */
 #include <math.h>
 #include <stdint.h>
@@ -79,6 +82,8 @@ typedef struct {
   int32_t max_seeds;
   /* beamline at z = 0 and its slopes, Sec. 3 */
   float x_b, y_b, tx_b, ty_b;
+  /* dip splitting: 0 in z order (GPU flavour, R5), 1 recursive (x86, R16) */
+  int32_t split_mode;
 } oc_params;
 
 /* ------------------------------------------------------------------------- */
@@ -271,6 +276,51 @@ static int oc_split(const uint32_t* N, int a, int b, const oc_params* p, int gas
   return n;
 }
 
+/* A maximum of N on [a, b]: a maximal run of equal bins higher than the bins
+ * next to it inside [a, b] (the ends count as lower); its position is the
+ * run's first bin. */
+static int oc_is_max_start(const uint32_t* N, int a, int b, int i, int* end) {
+  if (i > a && N[i - 1] >= N[i]) return 0;          /* not the run's first bin, or lower */
+  int q = i;
+  while (q < b && N[q + 1] == N[i]) q++;
+  *end = q;
+  return q == b || N[q + 1] < N[i];
+}
+
+/* Recursive dip splitting (the x86 variant of Sec. 3.3, reading R16): the two
+ * largest maxima of [a, b] (lower position first on equal values), the
+ * smallest bin strictly between them (leftmost on ties); split there (the
+ * minimum goes left) if it is significant against the smaller of the two
+ * maxima and both sides hold the minimal integral, then split both sides the
+ * same way; otherwise [a, b] is one piece. */
+static int oc_split_recursive(const uint32_t* N, int a, int b, const oc_params* p, int gas_bin,
+                              oc_range* out, int cap, int n) {
+  int m1 = -1, m2 = -1;                            /* positions of the two largest maxima */
+  for (int i = a; i <= b; ++i) {
+    int end;
+    if (!oc_is_max_start(N, a, b, i, &end)) continue;
+    if (m1 < 0 || N[i] > N[m1]) { m2 = m1; m1 = i; }
+    else if (m2 < 0 || N[i] > N[m2]) m2 = i;
+    i = end;
+  }
+  if (m2 >= 0) {
+    int lo = m1 < m2 ? m1 : m2, hi = m1 < m2 ? m2 : m1;
+    int m = -1;
+    for (int i = lo + 1; i < hi; ++i)
+      if (m < 0 || N[i] < N[m]) m = i;
+    uint64_t lower = N[m1] < N[m2] ? N[m1] : N[m2];
+    if (m >= 0 && (uint64_t)p->dip_den * (uint64_t)N[m] < (uint64_t)p->dip_num * lower) {
+      uint64_t T = oc_min_integral(oc_is_gas_bin(m, gas_bin), p);
+      if (oc_sum(N, a, m) >= T && oc_sum(N, m + 1, b) >= T) {
+        n = oc_split_recursive(N, a, m, p, gas_bin, out, cap, n);
+        return oc_split_recursive(N, m + 1, b, p, gas_bin, out, cap, n);
+      }
+    }
+  }
+  if (n < cap) { out[n].lo = a; out[n].hi = b; }
+  return n + 1;
+}
+
 typedef struct {
   int32_t lo, hi, bin;
   float x, y, z;
@@ -308,7 +358,8 @@ int oc_clusters_from_hist(const uint32_t* N, const oc_params* p, oc_seed* seeds,
     int a = i;
     while (i + 1 < nbins && N[i + 1] > p->bin_threshold) i++;
     int b = i;
-    int np = oc_split(N, a, b, p, gas_bin, pieces, 4096);
+    int np = p->split_mode == 1 ? oc_split_recursive(N, a, b, p, gas_bin, pieces, 4096, 0)
+                                : oc_split(N, a, b, p, gas_bin, pieces, 4096);
     if (np > 4096) np = 4096;
     for (int q = 0; q < np; ++q) {
       int lo = pieces[q].lo, hi = pieces[q].hi;

@@ -278,3 +278,58 @@ def test_seed_xy_on_beamline():
             assert f["x"][e, k] == np.float32(np.float32(0.5) + np.float32(1e-3) * z)
             assert f["y"][e, k] == np.float32(np.float32(-0.25) + np.float32(-2e-3) * z)
     assert oracle.seeds_from_hist(h, p)["n"] == 1
+
+
+# --- the x86 flavour: recursive splitting (reading R16) ---------------------
+
+P_REC = oracle.default_params(split_mode=1)
+
+
+def _pieces(h, p):
+    s = oracle.seeds_from_hist(h, p)
+    return [(int(a), int(b)) for a, b in zip(s["lo"], s["hi"])]
+
+
+def test_recursive_split_looks_at_the_two_largest_maxima():
+    """N = 8000, 6000, 10000, 8000, 10000.  In z order the first dip (6000)
+    is significant against min(8000, 10000) (30000 < 32000) and both sides hold
+    2.5 tracks, so the GPU flavour splits [0,1] | [2,4]; the dip 8000 between
+    the last two maxima is not (40000 < 40000 fails).  The x86 flavour looks
+    only between the two largest maxima (bins 2 and 4), finds 8000, and keeps
+    one piece."""
+    h = hist_with(place(2000, [8000, 6000, 10000, 8000, 10000]))
+    assert _pieces(h, P) == [(2000, 2001), (2002, 2004)]
+    assert _pieces(h, P_REC) == [(2000, 2004)]
+
+
+def test_recursive_split_recurses_on_both_sides():
+    """N = 4000, 6000, 4000, 6000, 2000, 10000, 300, 4000.  The two largest
+    maxima are 10000 (bin 5) and the first 6000 (bin 1, lower position on the
+    tie); the smallest bin between them is 2000 (bin 4): significant and both
+    sides hold 2.5 tracks (22000 and 14300), so split after bin 4.  Left
+    [0,4]: maxima 6000 at bins 1 and 3, minimum 4000 between, significant but
+    the right side (6000 + 2000) is below 2.5 tracks: no split.  Right [5,7]:
+    maxima 10000 and 4000, dip 300, right side 4000 too small: no split."""
+    h = hist_with(place(2000, [4000, 6000, 4000, 6000, 2000, 10000, 300, 4000]))
+    assert _pieces(h, P_REC) == [(2000, 2004), (2005, 2007)]
+    assert _pieces(h, P) == [(2000, 2002), (2003, 2007)]
+
+
+def test_recursive_split_agrees_on_single_peaks_and_clear_pairs():
+    """One maximum: one piece in both flavours; two well separated maxima with
+    a deep dip: the same split in both."""
+    one = hist_with(place(3000, [1000, 3000, 6000, 9000, 6000, 3000, 1000]))
+    assert _pieces(one, P_REC) == _pieces(one, P) == [(3000, 3006)]
+    two = hist_with(place(3000, [2000, 6000, 12000, 6000, 1000, 6000, 12000, 6000, 2000]))
+    assert _pieces(two, P_REC) == _pieces(two, P) == [(3000, 3004), (3005, 3008)]
+
+
+def test_recursive_split_splits_each_side_again():
+    """Three equal peaks with deep dips: the first split lies between the
+    first two maxima (equal values: lower positions first), and the right side
+    is split again between its two maxima; both flavours give three pieces."""
+    h = hist_with(place(2000, [2000, 6000, 12000, 6000, 1000, 6000, 12000, 6000, 1500, 6000, 12000,
+                               6000, 2000]))
+    want = [(2000, 2004), (2005, 2008), (2009, 2012)]
+    assert _pieces(h, P_REC) == want
+    assert _pieces(h, P) == want
