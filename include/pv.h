@@ -63,6 +63,10 @@ extern "C" {
 #define PV_ACCUM_KAHAN 1   /* compensated binary32 (error-free transformations) */
 #define PV_ACCUM_FP64 2    /* binary64 sums, reduction and solve (binary32 per-track terms) */
 
+/* dip splitting of proto-clusters (Sec. 3.3) */
+#define PV_SPLIT_ZORDER 0     /* GPU flavour: minima in z order (default) */
+#define PV_SPLIT_RECURSIVE 1  /* x86 flavour: smallest minimum between the two largest maxima, recursively */
+
 /* execution path */
 #define PV_PATH_FUSED 0    /* bucketed persistent kernels, shared-memory histograms */
 #define PV_PATH_PLAIN 1    /* one kernel per step, global-memory histograms */
@@ -98,6 +102,8 @@ typedef struct {
   float mv_dz_tol;                  /* convergence |dz| (Sec. 3.5, GPU rule): 0.0005 mm */
   float mv_w_assoc;                 /* weight from which a track counts for a vertex: 0.5 */
   float mv_dup_sep2;                /* duplicates: dz^2 < mv_dup_sep2 (C_zz + C_zz') (Sec. 3.5): 25 */
+  int32_t split_mode;               /* PV_SPLIT_*: default PV_SPLIT_ZORDER */
+  int32_t reserved2;                /* 0 */
 } pv_config;
 
 /* Tracks in structure-of-arrays layout (Sec. 5, x86: one contiguous array per

@@ -263,6 +263,7 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
     return PV_ERR_ARG;
   if (cfg.path != PV_PATH_FUSED && cfg.path != PV_PATH_PLAIN) return PV_ERR_ARG;
   if (!(cfg.min_integral_pp >= 0.0f) || !(cfg.min_integral_gas >= 0.0f)) return PV_ERR_ARG;
+  if (cfg.split_mode != PV_SPLIT_ZORDER && cfg.split_mode != PV_SPLIT_RECURSIVE) return PV_ERR_ARG;
   if (!(cfg.mv_chi2_cut > 0.0f) || !(cfg.mv_dz_tol >= 0.0f) || !(cfg.mv_w_assoc > 0.0f) ||
       !(cfg.mv_w_assoc <= 1.0f) || !(cfg.mv_dup_sep2 >= 0.0f))
     return PV_ERR_ARG;
@@ -289,6 +290,7 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
   C->mv_dz_tol = cfg.mv_dz_tol;
   C->mv_w_assoc = cfg.mv_w_assoc;
   C->mv_dup_sep2 = cfg.mv_dup_sep2;
+  C->split_mode = cfg.split_mode;
   C->thr = cfg.bin_threshold;
   C->t_pp = static_cast<uint32_t>(std::llround(static_cast<double>(cfg.min_integral_pp) * PV_ONE));
   C->t_gas = static_cast<uint32_t>(std::llround(static_cast<double>(cfg.min_integral_gas) * PV_ONE));
@@ -577,6 +579,8 @@ void pv_config_default(pv_config* c) {
   c->mv_dz_tol = 0.0005f;
   c->mv_w_assoc = 0.5f;
   c->mv_dup_sep2 = 25.0f;
+  c->split_mode = PV_SPLIT_ZORDER;
+  c->reserved2 = 0;
 }
 
 int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** out) {

@@ -49,6 +49,7 @@ struct Consts {
   // multi-vertex fit
   float mv_ecut;            // exp(-chi2_cut / 2)
   float mv_dz_tol, mv_w_assoc, mv_dup_sep2;
+  int32_t split_mode;       // PV_SPLIT_*
 };
 
 // ---------------------------------------------------------------------------
@@ -270,6 +271,86 @@ __host__ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t to
   emit(s, b, total - pre_s, iL);
 }
 
+// The x86 flavour of the dip splitting (Sec. 3.3): the smallest bin between
+// the two largest maxima of [a, b] (a maximum is a run of equal bins higher
+// than its neighbours inside [a, b]; equal maxima by lower position; leftmost
+// minimum), split there when the dip is significant against the smaller
+// maximum and both sides hold the minimal integral, then the same on each
+// side.  Calls emit(lo, hi, integral, im) per piece in z order.  Pieces come
+// out in z order, so a pending right-hand side starts one bin after the last
+// piece emitted and only its last bin waits on the stack.  The stack holds
+// kRecDepth entries; a deeper nesting (each pending side holds at least the
+// smaller minimal integral, so it needs a proto-cluster of more than
+// kRecDepth x 1.75 tracks' weight arranged as a nested comb) emits the
+// remaining range whole.
+constexpr int kRecDepth = 256;
+
+template <class Emit>
+__host__ __device__ void split_recursive(const uint32_t* N, int a, int b, const Consts& C,
+                                         Emit&& emit) {
+  int16_t st_hi[kRecDepth];
+  int sp = 0;
+  int lo = a, hi = b;
+  for (;;) {
+    int m1 = -1, m2 = -1;
+    for (int i = lo; i <= hi;) {
+      int q = i;
+      while (q < hi && N[q + 1] == N[i]) ++q;
+      const bool left_lower = i == lo || N[i - 1] < N[i];
+      const bool right_lower = q == hi || N[q + 1] < N[i];
+      if (left_lower && right_lower) {
+        if (m1 < 0 || N[i] > N[m1]) {
+          m2 = m1;
+          m1 = i;
+        } else if (m2 < 0 || N[i] > N[m2]) {
+          m2 = i;
+        }
+      }
+      i = q + 1;
+    }
+    bool split = false;
+    int m = -1;
+    if (m2 >= 0 && sp < kRecDepth) {
+      const int l = m1 < m2 ? m1 : m2, h = m1 < m2 ? m2 : m1;
+      for (int i = l + 1; i < h; ++i)
+        if (m < 0 || N[i] < N[m]) m = i;
+      const uint32_t lower = N[m1] < N[m2] ? N[m1] : N[m2];
+      if (m >= 0 &&
+          static_cast<uint64_t>(C.dip_den) * N[m] < static_cast<uint64_t>(C.dip_num) * lower) {
+        const uint64_t T = (m < C.gas_bin) ? C.t_gas : C.t_pp;
+        uint64_t left = 0, right = 0;
+        for (int i = lo; i <= m; ++i) left += N[i];
+        for (int i = m + 1; i <= hi; ++i) right += N[i];
+        split = left >= T && right >= T;
+      }
+    }
+    if (split) {
+      st_hi[sp++] = static_cast<int16_t>(hi);
+      hi = m;
+      continue;
+    }
+    uint64_t integral = 0;
+    int im = lo;
+    for (int i = lo; i <= hi; ++i) {
+      integral += N[i];
+      if (N[i] > N[im]) im = i;
+    }
+    emit(lo, hi, integral, im);
+    if (sp == 0) break;
+    lo = hi + 1;
+    hi = st_hi[--sp];
+  }
+}
+
+// The pieces of proto-cluster [a, b] in the chosen flavour.
+template <int kSplit, class Emit>
+__host__ __device__ __forceinline__ void split_pieces(const uint32_t* N, int a, int b,
+                                                      uint64_t total, const Consts& C,
+                                                      Emit&& emit) {
+  if constexpr (kSplit == PV_SPLIT_RECURSIVE) split_recursive(N, a, b, C, emit);
+  else split_walk(N, a, b, total, C, emit);
+}
+
 // A piece is a seed cluster if it holds the minimal integral of the region of
 // its maximum bin im.
 __host__ __device__ __forceinline__ bool keep_piece(uint64_t integral, int im, const Consts& C) {
@@ -302,7 +383,7 @@ __device__ __forceinline__ uint32_t bin_or_zero(const uint32_t* N, int j, const 
 // bins; otherwise every tile is scanned.  pc_lo / pc_hi are a kRunRing-entry ring
 // in shared memory.  Writes up to cap seeds into S in z order and returns the
 // number found (which may exceed cap).  All 32 lanes must call it.
-template <bool kSeedZ>
+template <bool kSeedZ, int kSplit = PV_SPLIT_ZORDER>
 __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
                                       SeedOut* S, int cap, int16_t* pc_lo, int16_t* pc_hi) {
   const int lane = threadIdx.x & 31;
@@ -341,7 +422,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     const bool walk = lane < count && total >= t_min;
     int kept = 0, lo1 = 0, hi1 = 0, im1 = 0;
     if (walk) {
-      split_walk(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
+      split_pieces<kSplit>(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
         if (keep_piece(integral, im, C)) {
           if (kept == 0) { lo1 = lo; hi1 = hi; im1 = im; }
           ++kept;
@@ -358,7 +439,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     if (kept == 1 && pos < cap) {
       put(pos, lo1, hi1, im1);
     } else if (kept > 1 && pos < cap) {
-      split_walk(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
+      split_pieces<kSplit>(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
         if (keep_piece(integral, im, C)) {
           if (pos < cap) put(pos, lo, hi, im);
           ++pos;

@@ -217,7 +217,7 @@ __device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tr
 //           position is left in the output row, which the fit overwrites.
 // kFit:     seeds and assignments from the caller, then fit inputs and work.
 
-template <int MODE, int NT>
+template <int MODE, int NT, int SPLIT = PV_SPLIT_ZORDER>
 __global__ void __launch_bounds__(NT)
 find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -304,7 +304,7 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       if (warp == 0) {
         // the seed position is computed here only when it is the output;
         // otherwise the fit kernel derives it from the bins around the maximum
-        int K = warp_find_seeds<MODE == kFind>(hist, tmask, C, S, O.cap, pc_lo, pc_hi);
+        int K = warp_find_seeds<MODE == kFind, SPLIT>(hist, tmask, C, S, O.cap, pc_lo, pc_hi);
         if (lane == 0) misc[2] = K;
       }
       __syncthreads();
@@ -863,14 +863,22 @@ int mv_blocks_per_sm(void) {
 // ---------------------------------------------------------------------------
 // launch plumbing: kernel instantiations by block size
 
-template <int MODE, int NT>
-static cudaError_t setup_find(int nbins) {
-  cudaError_t err = cudaFuncSetAttribute(find_kernel<MODE, NT>,
+template <int MODE, int NT, int SPLIT>
+static cudaError_t setup_find_split(int nbins) {
+  cudaError_t err = cudaFuncSetAttribute(find_kernel<MODE, NT, SPLIT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)fused_smem_bytes(nbins, MODE));
   if (err != cudaSuccess) return err;
-  return cudaFuncSetAttribute(find_kernel<MODE, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  return cudaFuncSetAttribute(find_kernel<MODE, NT, SPLIT>,
+                              cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
+}
+
+template <int MODE, int NT>
+static cudaError_t setup_find(int nbins) {
+  cudaError_t err = setup_find_split<MODE, NT, PV_SPLIT_ZORDER>(nbins);
+  if (err != cudaSuccess) return err;
+  return setup_find_split<MODE, NT, PV_SPLIT_RECURSIVE>(nbins);
 }
 
 template <int NT>
@@ -950,7 +958,10 @@ template <int MODE, int NT>
 static void launch_find_nt(int grid, size_t sm, cudaStream_t st, const Consts& C,
                            const TrackPtrs& T, const SeedPtrs& S, const OutPtrs& O,
                            const TrackScratch& ws) {
-  find_kernel<MODE, NT><<<grid, NT, sm, st>>>(C, T, S, O, ws);
+  if (C.split_mode == PV_SPLIT_RECURSIVE)
+    find_kernel<MODE, NT, PV_SPLIT_RECURSIVE><<<grid, NT, sm, st>>>(C, T, S, O, ws);
+  else
+    find_kernel<MODE, NT, PV_SPLIT_ZORDER><<<grid, NT, sm, st>>>(C, T, S, O, ws);
 }
 
 template <int MODE>
@@ -1009,6 +1020,7 @@ __global__ void plain_hist_kernel(Consts C, TrackPtrs T, const float* zpoca, con
     if (center[i] >= 0) fill_profile(h, zpoca[i], sigma[i], j0[i], j1[i], C);
 }
 
+template <int SPLIT>
 __global__ void __launch_bounds__(32)
 plain_peaks_kernel(Consts C, TrackPtrs T, const uint32_t* hist, int cap, int32_t* seed_n,
                    int32_t* seed_lo, int32_t* seed_hi, int32_t* seed_bin, float* seed_z,
@@ -1022,8 +1034,8 @@ plain_peaks_kernel(Consts C, TrackPtrs T, const uint32_t* hist, int cap, int32_t
     if (lane == 0) { seed_n[e] = 0; ev_status[e] = PV_EV_BAD_OFFSETS; }
     return;
   }
-  int K = warp_find_seeds<true>(hist + static_cast<size_t>(e) * C.nbins, nullptr, C, &S, cap, pc_lo,
-                                pc_hi);
+  int K = warp_find_seeds<true, SPLIT>(hist + static_cast<size_t>(e) * C.nbins, nullptr, C, &S,
+                                       cap, pc_lo, pc_hi);
   int Ks = K < cap ? K : cap;
   for (int k = lane; k < Ks; k += 32) {
     size_t q = static_cast<size_t>(e) * kMaxSeeds + k;
@@ -1157,8 +1169,14 @@ cudaError_t launch_plain_find(const Consts& C, const TrackPtrs& T, const OutPtrs
                               const PlainScratch& ws, cudaStream_t st, int* n_launches) {
   cudaError_t err = launch_histogram(C, T, ws.hist, ws, st, n_launches);
   if (err != cudaSuccess) return err;
-  plain_peaks_kernel<<<T.n_events, 32, 0, st>>>(C, T, ws.hist, O.cap, ws.seed_n, ws.seed_lo,
-                                                ws.seed_hi, ws.seed_bin, ws.seed_z, ws.ev_status);
+  if (C.split_mode == PV_SPLIT_RECURSIVE)
+    plain_peaks_kernel<PV_SPLIT_RECURSIVE><<<T.n_events, 32, 0, st>>>(
+        C, T, ws.hist, O.cap, ws.seed_n, ws.seed_lo, ws.seed_hi, ws.seed_bin, ws.seed_z,
+        ws.ev_status);
+  else
+    plain_peaks_kernel<PV_SPLIT_ZORDER><<<T.n_events, 32, 0, st>>>(
+        C, T, ws.hist, O.cap, ws.seed_n, ws.seed_lo, ws.seed_hi, ws.seed_bin, ws.seed_z,
+        ws.ev_status);
   plain_assoc_kernel<<<T.n_events, 256, 0, st>>>(C, T, O, ws.center, ws.cid, ws.seed_n, ws.seed_lo,
                                                  ws.seed_hi, ws.seed_bin, ws.seed_z, ws.ev_status);
   *n_launches += 2;

@@ -279,3 +279,27 @@ def test_pp_plus_gas_overlay(pv, tilted):
     fit = oracle.fit_batch(batch, ref, p)
     G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref, beam=beam),
                        cond=(batch, ref, p))
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_recursive_split_flavour(pv, path):
+    """The x86 flavour of the peak search (Sec. 3.3, reading R16) through the
+    fused and the plain path: seeds bit-exact and the fit within tolerance on
+    the nominal workload and the pp + p-gas overlay (both regions' minimal
+    integrals).  The two flavours part on a few percent of the events."""
+    cfg = dict(split_mode=pv.SPLIT_RECURSIVE)
+    if path == "plain":
+        cfg["path"] = pv.PATH_PLAIN
+    for batch in (synthetic.workload_nominal(n_events=1500, seed=14),
+                  synthetic.workload_overlay(n_events=800, seed=13)):
+        ctx = pv.Context(device=0, **cfg)
+        s, v = G.gpu_find_fit(ctx, batch)
+        ctx.close()
+        p = oracle.default_params(split_mode=1)
+        ref = oracle.find_batch(batch, p)
+        G.assert_find_equal(s, ref, batch)
+        ref0 = oracle.find_batch(batch, oracle.default_params())
+        assert (ref0["n"] != ref["n"]).any()
+        fit = oracle.fit_batch(batch, ref, p)
+        G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref, **cfg),
+                           cond=(batch, ref, p))

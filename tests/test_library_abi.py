@@ -124,6 +124,19 @@ def test_default_config_is_the_papers(lib):
     # the unstated settings agree between library and oracle
     p = oracle.default_params()
     assert (c.bin_threshold, c.dip_num, c.dip_den) == (p.bin_threshold, p.dip_num, p.dip_den)
+    assert c.split_mode == p.split_mode == pv.SPLIT_ZORDER
+
+
+@pytest.mark.parametrize("field,value", [("split_mode", 2), ("split_mode", -1), ("dz", 0.0),
+                                         ("mv_chi2_cut", 0.0)])
+def test_invalid_config_is_refused_before_the_device(lib, field, value):
+    """pv_init checks the configuration before it looks for a device."""
+    import paper_2412_14966_gb300 as pv
+    cfg = pv.default_config(**{field: value})
+    beam = pv.pv_beamline(0.0, 0.0, 0.0, 0.0)
+    h = ctypes.c_void_p()
+    assert lib.pv_init(ctypes.byref(cfg), ctypes.byref(beam), 0, ctypes.byref(h)) == pv.PV_ERR_ARG
+    assert not h.value
 
 
 def test_strerror(lib):

@@ -1,5 +1,5 @@
-// Host-side harness around the library's peak-search walk (split_walk and
-// keep_piece in pv_device.cuh), so CPU tests can compare it with the oracle on
+// Host-side harness around the library's peak search (split_walk,
+// split_recursive and keep_piece in pv_device.cuh), so CPU tests can compare it with the oracle on
 // many histograms.  Test code only: proto-clusters are found with a plain loop
 // and every proto-cluster is walked (no early skip).
 #include <cstdint>
@@ -7,8 +7,8 @@
 #include "pv_device.cuh"
 
 extern "C" int harness_seeds(const uint32_t* N, int nbins, uint32_t thr, uint32_t t_pp,
-                             uint32_t t_gas, int dip_num, int dip_den, int gas_bin, int* lo,
-                             int* hi, int* bin, int cap) {
+                             uint32_t t_gas, int dip_num, int dip_den, int gas_bin,
+                             int split_mode, int* lo, int* hi, int* bin, int cap) {
   pvdev::Consts C{};
   C.nbins = nbins;
   C.thr = thr;
@@ -25,7 +25,7 @@ extern "C" int harness_seeds(const uint32_t* N, int nbins, uint32_t thr, uint32_
     const int b = i;
     uint64_t total = 0;
     for (int j = a; j <= b; ++j) total += N[j];
-    pvdev::split_walk(N, a, b, total, C, [&](int l, int h, uint64_t integral, int im) {
+    auto emit = [&](int l, int h, uint64_t integral, int im) {
       if (pvdev::keep_piece(integral, im, C)) {
         if (n < cap) {
           lo[n] = l;
@@ -34,7 +34,11 @@ extern "C" int harness_seeds(const uint32_t* N, int nbins, uint32_t thr, uint32_
         }
         ++n;
       }
-    });
+    };
+    if (split_mode == PV_SPLIT_RECURSIVE)
+      pvdev::split_pieces<PV_SPLIT_RECURSIVE>(N, a, b, total, C, emit);
+    else
+      pvdev::split_pieces<PV_SPLIT_ZORDER>(N, a, b, total, C, emit);
   }
   return n;
 }
