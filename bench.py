@@ -463,6 +463,23 @@ def run_ours(args):
     multi_ms = ms_.elapsed_time(me_) / multi_steps
     del mouts
 
+    # the x86 flavour of steps (b) and (c) (template profiles, recursive dip
+    # split) with the same fused fit, same timing
+    x86 = pv.Context(device=local, use_graph=1, split_mode=pv.SPLIT_RECURSIVE,
+                     profile_mode=pv.PROFILE_TEMPLATE)
+    for i in range(max(args.warmup, 1)):
+        step(i, x86)
+    torch.cuda.synchronize()
+    x86_steps = max(1, min(args.steps, 200))
+    xs_, xe_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    xs_.record(stream)
+    for i in range(x86_steps):
+        step(i, x86)
+    xe_.record(stream)
+    torch.cuda.synchronize()
+    x86_ms = xs_.elapsed_time(xe_) / x86_steps
+    x86.close()
+
     # end to end through the C ABI with host buffers (pinned), copies included
     host = pv.Tracks.from_host(batch, pinned=True)
     hout = pv.Vertices.empty(E, NT, host=True, pinned=True, bins=False)
@@ -505,6 +522,9 @@ def run_ours(args):
         "multi": {"value": E * world / (multi_ms / 1e3), "ms_per_step": multi_ms,
                   "path": "find kernel + multi-vertex fit kernel (pv_fit_multi, GPU flavour "
                           "of the fit: implicit association, duplicate removal)"},
+        "x86_flavour": {"value": E * world / (x86_ms / 1e3), "ms_per_step": x86_ms,
+                        "path": "fused find + fit with template profiles and the recursive "
+                                "dip split (Sec. 3.2-3.3, x86 flavour)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "pv_run_host (pinned host buffers)"},
         "clocks": clk,

@@ -63,6 +63,10 @@ extern "C" {
 #define PV_ACCUM_KAHAN 1   /* compensated binary32 (error-free transformations) */
 #define PV_ACCUM_FP64 2    /* binary64 sums, reduction and solve (binary32 per-track terms) */
 
+/* histogram profile (Sec. 3.2) */
+#define PV_PROFILE_CUBIC 0     /* GPU flavour: quantised cubic CDF (default) */
+#define PV_PROFILE_TEMPLATE 1  /* x86 flavour: template histograms chosen by sigma_poca */
+
 /* dip splitting of proto-clusters (Sec. 3.3) */
 #define PV_SPLIT_ZORDER 0     /* GPU flavour: minima in z order (default) */
 #define PV_SPLIT_RECURSIVE 1  /* x86 flavour: smallest minimum between the two largest maxima, recursively */
@@ -103,7 +107,7 @@ typedef struct {
   float mv_w_assoc;                 /* weight from which a track counts for a vertex: 0.5 */
   float mv_dup_sep2;                /* duplicates: dz^2 < mv_dup_sep2 (C_zz + C_zz') (Sec. 3.5): 25 */
   int32_t split_mode;               /* PV_SPLIT_*: default PV_SPLIT_ZORDER */
-  int32_t reserved2;                /* 0 */
+  int32_t profile_mode;             /* PV_PROFILE_*: default PV_PROFILE_CUBIC */
 } pv_config;
 
 /* Tracks in structure-of-arrays layout (Sec. 5, x86: one contiguous array per

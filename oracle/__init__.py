@@ -48,7 +48,7 @@ class Params(C.Structure):
         ("max_r_beam", C.c_double),
         ("max_seeds", C.c_int32),
         ("x_b", C.c_float), ("y_b", C.c_float), ("tx_b", C.c_float), ("ty_b", C.c_float),
-        ("split_mode", C.c_int32),
+        ("split_mode", C.c_int32), ("profile_mode", C.c_int32),
     ]
 
 
@@ -88,6 +88,7 @@ def default_params(**kw) -> Params:
         max_seeds=64,
         x_b=0.0, y_b=0.0, tx_b=0.0, ty_b=0.0,
         split_mode=0,                                # Sec. 3.3: GPU (z order); 1 = x86 (R16)
+        profile_mode=0,                              # Sec. 3.2: GPU (cubic CDF); 1 = x86 templates (R17)
     )
     for k, v in kw.items():
         setattr(p, k, v)
@@ -141,6 +142,9 @@ def lib():
                                    dp, dp, dp, dp, dp, dp, ip, ip, ip]
         L.oc_fit_tracks.argtypes = [arr11, C.c_int64, C.c_float, C.c_float, C.c_float, pp,
                                     dp, dp, dp, dp, ip, ip, ip]
+        L.oc_template_classes.restype = C.c_int
+        L.oc_template_table.argtypes = [pp, dp, dp, ip, ip, ip, C.c_int]
+        L.oc_template_table.restype = C.c_int
         L.oc_seeds_from_hist.argtypes = [up, pp, ip, ip, ip, fp, C.c_int]
         L.oc_seeds_from_hist.restype = C.c_int
         L.oc_associate_bins.argtypes = [ip, C.c_int64, ip, ip, ip, C.c_int, pp, ip, ip]
@@ -203,6 +207,22 @@ def track_profile(zpoca: float, sigma: float, p: Params):
     if n < 0:
         raise ValueError("profile window larger than the histogram")
     return int(first.value), w[:n].copy()
+
+
+def template_table(p: Params) -> dict:
+    """The x86 flavour's template profiles (reading R17): per class its sigma,
+    the lowest sigma_poca it takes, its half-width H and its quantised
+    cumulative values Q[0 .. 2H+1] at the bin edges around the centre bin."""
+    L = lib()
+    K = L.oc_template_classes()
+    sig = np.zeros(K, np.float64); bound = np.zeros(K, np.float64)
+    half = np.zeros(K, np.int32); first = np.zeros(K, np.int32)
+    total = L.oc_template_table(C.byref(p), None, None, None, None, None, 0)
+    q = np.zeros(total, np.int32)
+    L.oc_template_table(C.byref(p), _ptr(sig, C.c_double), _ptr(bound, C.c_double),
+                        _ptr(half, C.c_int32), _ptr(first, C.c_int32), _ptr(q, C.c_int32), total)
+    return {"sigma": sig, "bound": bound, "half": half,
+            "q": [q[first[k]:first[k] + 2 * half[k] + 2].copy() for k in range(K)]}
 
 
 def seeds_from_hist(hist: np.ndarray, p: Params, cap: int = 4096) -> dict:

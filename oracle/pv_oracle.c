@@ -41,6 +41,11 @@
  *   R16 the x86 dip splitting (split_mode 1): the smallest bin between the two
  *      largest maxima, with the significance and integral tests of R5, applied
  *      recursively to both sides (see oc_split_recursive).
+ *   R17 the x86 profile (profile_mode 1): a track adds the template of its
+ *      sigma_poca class, centred on the bin of its z_poca.  Class k has
+ *      sigma_k = 0.01 mm * 2^(k/4), k = 0 .. 40, and holds the sigma_poca from
+ *      sigma_{k-1} 2^(1/8) up; its template is the exact Gaussian integral over
+ *      each bin for a mean at the bin centre, quantised like R3 (see oc_tpl_build).
  */
 #include <math.h>
 #include <stdint.h>
@@ -84,6 +89,8 @@ typedef struct {
   float x_b, y_b, tx_b, ty_b;
   /* dip splitting: 0 in z order (GPU flavour, R5), 1 recursive (x86, R16) */
   int32_t split_mode;
+  /* profile: 0 cubic CDF (GPU flavour, R3), 1 templates chosen by sigma (x86, R17) */
+  int32_t profile_mode;
 } oc_params;
 
 /* ------------------------------------------------------------------------- */
@@ -114,11 +121,87 @@ static float oc_edge_f32(int j, const oc_params* p) {
 typedef struct {
   float zpoca, sigma;
   int32_t center, j0, j1, filled;
+  int32_t tcls;                                    /* template class (R17), else -1 */
 } oc_prep32;
+
+/* ------------------------------------------------------------------------- */
+/* template profiles of the x86 flavour, Sec. 3.2, reading R17               */
+
+#define OC_TPL_CLASSES 41
+#define OC_TPL_SIGMA0 0.01                      /* mm: sigma of class 0 */
+#define OC_TPL_RATIO 1.189207115002721          /* 2^(1/4) between classes */
+#define OC_TPL_HALF_RATIO 1.0905077326652577    /* 2^(1/8): class boundaries */
+#define OC_TPL_MAX_HALF 1024
+
+typedef struct {
+  double sigma[OC_TPL_CLASSES];   /* sigma_k */
+  double bound[OC_TPL_CLASSES];   /* lowest sigma_poca of class k (bound[0] = 0) */
+  int32_t half[OC_TPL_CLASSES];   /* H_k: the template covers bins c - H_k .. c + H_k */
+  int32_t first[OC_TPL_CLASSES];  /* where class k's cumulative values start in q */
+  int32_t* q;                     /* Q_k[i], i = 0 .. 2 H_k + 1, at edge (i - H_k - 1/2) dz */
+} oc_tpl;
+
+/* standard normal CDF */
+static double oc_phi(double x) { return 0.5 * erfc(-x * 0.70710678118654752440); }
+
+/* rint(ONE * Phi) at the edge (i - H - 1/2) dz from the centre of the bin */
+static long oc_tpl_q(int i, int H, double dz, double s) {
+  double x = ((double)(i - H) - 0.5) * dz / s;
+  return lrint((double)OC_ONE * oc_phi(x));
+}
+
+/* The templates: H_k is the smallest H whose outer edge holds a quantised
+ * CDF of 0; Q_k[0] = 0, Q_k[2 H_k + 1] = ONE and the interior edges hold the
+ * quantised Gaussian CDF, made non-decreasing.  Returns 0, -1 on failure. */
+static int oc_tpl_build(const oc_params* p, oc_tpl* t) {
+  double dz = (double)p->dz;
+  double s = OC_TPL_SIGMA0;
+  int total = 0;
+  for (int k = 0; k < OC_TPL_CLASSES; ++k) {
+    if (k > 0) {
+      t->bound[k] = s * OC_TPL_HALF_RATIO;
+      s = s * OC_TPL_RATIO;
+    } else {
+      t->bound[k] = 0.0;
+    }
+    t->sigma[k] = s;
+    int H = 0;
+    while (H < OC_TPL_MAX_HALF && oc_tpl_q(0, H, dz, s) != 0) H++;
+    t->half[k] = H;
+    t->first[k] = total;
+    total += 2 * H + 2;
+  }
+  t->q = (int32_t*)malloc(sizeof(int32_t) * (size_t)total);
+  if (!t->q) return -1;
+  for (int k = 0; k < OC_TPL_CLASSES; ++k) {
+    int H = t->half[k];
+    int32_t* q = t->q + t->first[k];
+    q[0] = 0;
+    for (int i = 1; i <= 2 * H; ++i) {
+      long v = oc_tpl_q(i, H, dz, t->sigma[k]);
+      if (v < 0) v = 0;
+      if (v > OC_ONE) v = OC_ONE;
+      if (v < q[i - 1]) v = q[i - 1];
+      q[i] = (int32_t)v;
+    }
+    q[2 * H + 1] = OC_ONE;
+  }
+  return 0;
+}
+
+static void oc_tpl_free(oc_tpl* t) { free(t->q); t->q = NULL; }
+
+/* class of sigma_poca: the last class whose lower bound it reaches */
+static int oc_tpl_class(float sigma, const oc_tpl* t) {
+  int k = 0;
+  for (int j = 1; j < OC_TPL_CLASSES; ++j)
+    if ((double)sigma >= t->bound[j]) k = j;
+  return k;
+}
 
 static void oc_prepare_f32(float x, float y, float z, float tx, float ty,
                            float cxx, float cxtx, float ctxtx,
-                           const oc_params* p, int nbins, oc_prep32* out) {
+                           const oc_params* p, const oc_tpl* tpl, int nbins, oc_prep32* out) {
   /* slopes relative to the beam */
   float dtx = tx - p->tx_b;
   float dty = ty - p->ty_b;
@@ -138,16 +221,24 @@ static void oc_prepare_f32(float x, float y, float z, float tx, float ty,
   out->center = -1;
   out->j0 = 0;
   out->j1 = -1;
+  out->tcls = -1;
   if (!(t2 > 0.0f)) return;
   if (!isfinite(zp) || !isfinite(sig)) return;
   int c = oc_bin_f32(zp, p, nbins);
   if (c < 0 || c >= nbins) return;
   float smax = (zp < p->z_gas) ? p->sigma_max_gas : p->sigma_max_pp;
   if (!(sig <= smax)) return;
-  float s = 2.23606797749979f * sig;
-  if (s < OC_S_MIN) s = 0.0f;
   out->filled = 1;
   out->center = c;
+  if (tpl) {                                       /* R17 */
+    int k = oc_tpl_class(sig, tpl);
+    out->tcls = k;
+    out->j0 = c - tpl->half[k];
+    out->j1 = c + tpl->half[k];
+    return;
+  }
+  float s = 2.23606797749979f * sig;
+  if (s < OC_S_MIN) s = 0.0f;
   out->j0 = oc_bin_f32(zp - s, p, nbins);
   out->j1 = oc_bin_f32(zp + s, p, nbins);
 }
@@ -188,7 +279,15 @@ static int32_t oc_quant_cdf(float u) {
 /* Per-bin integer weights of one filled track.  weights[k] belongs to bin
  * j0 + k, k = 0 .. j1 - j0.  Bins outside [0, nbins) are included here with
  * their weight; the caller drops them.  Returns the number of bins. */
-static int oc_profile_weights(const oc_prep32* t, const oc_params* p, uint32_t* weights, int cap) {
+static int oc_profile_weights(const oc_prep32* t, const oc_params* p, const oc_tpl* tpl,
+                              uint32_t* weights, int cap) {
+  if (tpl) {                                       /* R17: the class template */
+    const int32_t* q = tpl->q + tpl->first[t->tcls];
+    int n = 2 * tpl->half[t->tcls] + 1;
+    if (n > cap) return -1;
+    for (int i = 0; i < n; ++i) weights[i] = (uint32_t)(q[i + 1] - q[i]);
+    return n;
+  }
   float s = 2.23606797749979f * t->sigma;
   if (s < OC_S_MIN) s = 0.0f;
   float inv_s = (s > 0.0f) ? 1.0f / s : 0.0f;
@@ -580,18 +679,52 @@ int oc_gas_bin(const oc_params* p) { return oc_bin_f32(p->z_gas, p, oc_nbins(p))
 
 /* Step (a) in contract mode for n tracks (T = 11 SoA arrays in the order
  * x y z tx ty cxx cxtx ctxtx cyy cyty ctyty). */
+/* The templates of p's profile, or NULL for the cubic profile (built into *t). */
+static const oc_tpl* oc_tpl_for(const oc_params* p, oc_tpl* t) {
+  t->q = NULL;
+  if (p->profile_mode != 1) return NULL;
+  if (oc_tpl_build(p, t) != 0) abort();
+  return t;
+}
+
+/* Step (a) in contract mode for n tracks (T = 11 SoA arrays in the order
+ * x y z tx ty cxx cxtx ctxtx cyy cyty ctyty); j0, j1 bound the profile. */
 void oc_prepare_tracks_f32(const float* const* T, int64_t n, const oc_params* p,
                            float* zpoca, float* sigma, int32_t* center,
                            int32_t* j0, int32_t* j1, int32_t* filled) {
   int nbins = oc_nbins(p);
+  oc_tpl store;
+  const oc_tpl* tpl = oc_tpl_for(p, &store);
   for (int64_t t = 0; t < n; ++t) {
     oc_prep32 r;
     oc_prepare_f32(T[0][t], T[1][t], T[2][t], T[3][t], T[4][t], T[5][t], T[6][t], T[7][t],
-                   p, nbins, &r);
+                   p, tpl, nbins, &r);
     zpoca[t] = r.zpoca; sigma[t] = r.sigma; center[t] = r.center;
     j0[t] = r.j0; j1[t] = r.j1; filled[t] = r.filled;
   }
+  oc_tpl_free(&store);
 }
+
+/* The template table of the x86 profile (R17): per class sigma_k, its lowest
+ * sigma_poca, H_k and the start of its cumulative values in q (q may be NULL
+ * to ask for the size).  Returns the number of q entries. */
+int oc_template_table(const oc_params* p, double* sigma, double* bound, int32_t* half,
+                      int32_t* first, int32_t* q, int cap) {
+  oc_tpl t;
+  if (oc_tpl_build(p, &t) != 0) return -1;
+  int total = t.first[OC_TPL_CLASSES - 1] + 2 * t.half[OC_TPL_CLASSES - 1] + 2;
+  for (int k = 0; k < OC_TPL_CLASSES; ++k) {
+    if (sigma) sigma[k] = t.sigma[k];
+    if (bound) bound[k] = t.bound[k];
+    if (half) half[k] = t.half[k];
+    if (first) first[k] = t.first[k];
+  }
+  if (q && cap >= total) memcpy(q, t.q, sizeof(int32_t) * (size_t)total);
+  oc_tpl_free(&t);
+  return total;
+}
+
+int oc_template_classes(void) { return OC_TPL_CLASSES; }
 
 /* Step (a) in binary64, for error reports. */
 void oc_prepare_tracks_f64(const float* const* T, int64_t n, const oc_params* p,
@@ -607,36 +740,56 @@ void oc_prepare_tracks_f64(const float* const* T, int64_t n, const oc_params* p,
 int oc_track_profile(float zpoca, float sigma, const oc_params* p, int32_t* first,
                      uint32_t* weights, int cap) {
   int nbins = oc_nbins(p);
+  oc_tpl store;
+  const oc_tpl* tpl = oc_tpl_for(p, &store);
   oc_prep32 t;
   t.zpoca = zpoca;
   t.sigma = sigma;
-  float s = 2.23606797749979f * sigma;
-  if (s < OC_S_MIN) s = 0.0f;
-  t.j0 = oc_bin_f32(zpoca - s, p, nbins);
-  t.j1 = oc_bin_f32(zpoca + s, p, nbins);
+  if (tpl) {
+    t.tcls = oc_tpl_class(sigma, tpl);
+    t.j0 = oc_bin_f32(zpoca, p, nbins) - tpl->half[t.tcls];
+    t.j1 = t.j0 + 2 * tpl->half[t.tcls];
+  } else {
+    float s = 2.23606797749979f * sigma;
+    if (s < OC_S_MIN) s = 0.0f;
+    t.j0 = oc_bin_f32(zpoca - s, p, nbins);
+    t.j1 = oc_bin_f32(zpoca + s, p, nbins);
+  }
   *first = t.j0;
-  return oc_profile_weights(&t, p, weights, cap);
+  int n = oc_profile_weights(&t, p, tpl, weights, cap);
+  oc_tpl_free(&store);
+  return n;
 }
 
 /* Histogram of one event (nbins bins, cleared here). */
-void oc_event_histogram(const float* const* T, int64_t begin, int64_t end, const oc_params* p,
-                        uint32_t* hist, int32_t* center) {
+static void oc_event_histogram_t(const float* const* T, int64_t begin, int64_t end,
+                                 const oc_params* p, const oc_tpl* tpl, uint32_t* hist,
+                                 int32_t* center) {
   int nbins = oc_nbins(p);
+  int cap = nbins + 2 * OC_TPL_MAX_HALF + 8;
   memset(hist, 0, sizeof(uint32_t) * (size_t)nbins);
-  uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(nbins + 8));
+  uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)cap);
   for (int64_t t = begin; t < end; ++t) {
     oc_prep32 r;
     oc_prepare_f32(T[0][t], T[1][t], T[2][t], T[3][t], T[4][t], T[5][t], T[6][t], T[7][t],
-                   p, nbins, &r);
+                   p, tpl, nbins, &r);
     center[t - begin] = r.filled ? r.center : -1;
     if (!r.filled) continue;
-    int k = oc_profile_weights(&r, p, w, nbins + 8);
+    int k = oc_profile_weights(&r, p, tpl, w, cap);
     for (int q = 0; q < k; ++q) {
       int j = r.j0 + q;
       if (j >= 0 && j < nbins) hist[j] += w[q];
     }
   }
   free(w);
+}
+
+void oc_event_histogram(const float* const* T, int64_t begin, int64_t end, const oc_params* p,
+                        uint32_t* hist, int32_t* center) {
+  oc_tpl store;
+  const oc_tpl* tpl = oc_tpl_for(p, &store);
+  oc_event_histogram_t(T, begin, end, p, tpl, hist, center);
+  oc_tpl_free(&store);
 }
 
 /* Steps (a)-(d1) for a batch of events.
@@ -653,11 +806,13 @@ int oc_find_batch(const float* const* T, const int64_t* offsets, int32_t n_event
   uint32_t* hist = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nbins);
   oc_seed* seeds = (oc_seed*)malloc(sizeof(oc_seed) * (size_t)(cap > 0 ? cap : 1));
   int32_t* keep = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+  oc_tpl store;
+  const oc_tpl* tpl = oc_tpl_for(p, &store);
   for (int32_t e = 0; e < n_events; ++e) {
     int64_t b = offsets[e], en = offsets[e + 1];
     int64_t n = en - b;
     int32_t* center = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-    oc_event_histogram(T, b, en, p, hist, center);
+    oc_event_histogram_t(T, b, en, p, tpl, hist, center);
     if (hist_out) memcpy(hist_out + (size_t)e * nbins, hist, sizeof(uint32_t) * (size_t)nbins);
     int K = oc_clusters_from_hist(hist, p, seeds, cap);
     event_status[e] = 0;
@@ -677,6 +832,7 @@ int oc_find_batch(const float* const* T, const int64_t* offsets, int32_t n_event
   free(hist);
   free(seeds);
   free(keep);
+  oc_tpl_free(&store);
   return 0;
 }
 

@@ -29,6 +29,7 @@ MAX_SEEDS = 64
 ACCUM_FP32, ACCUM_KAHAN, ACCUM_FP64 = 0, 1, 2
 PATH_FUSED, PATH_PLAIN = 0, 1
 SPLIT_ZORDER, SPLIT_RECURSIVE = 0, 1
+PROFILE_CUBIC, PROFILE_TEMPLATE = 0, 1
 
 EXPORTED = (
     "pv_config_default", "pv_init", "pv_destroy", "pv_find_batch", "pv_fit_batch",
@@ -66,7 +67,7 @@ class pv_config(C.Structure):
         ("use_graph", C.c_int32), ("reserved", C.c_int32),
         ("pool_bytes", C.c_uint64), ("max_spin_ns", C.c_uint64),
         ("mv_chi2_cut", C.c_float), ("mv_dz_tol", C.c_float), ("mv_w_assoc", C.c_float),
-        ("mv_dup_sep2", C.c_float), ("split_mode", C.c_int32), ("reserved2", C.c_int32),
+        ("mv_dup_sep2", C.c_float), ("split_mode", C.c_int32), ("profile_mode", C.c_int32),
     ]
 
 

@@ -219,6 +219,7 @@ struct pv_ctx {
   std::map<std::string, cudaGraphExec_t> graphs;
   cudaStream_t capture_stream = nullptr;
   DevBuf fused_ws, plain_ws, mv_ws;
+  DevBuf tpl;                         // template profiles (profile_mode TEMPLATE)
   int mv_per_sm = 0;
   // host-buffer entry point staging
   DevBuf host_in, host_out;
@@ -264,6 +265,8 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
   if (cfg.path != PV_PATH_FUSED && cfg.path != PV_PATH_PLAIN) return PV_ERR_ARG;
   if (!(cfg.min_integral_pp >= 0.0f) || !(cfg.min_integral_gas >= 0.0f)) return PV_ERR_ARG;
   if (cfg.split_mode != PV_SPLIT_ZORDER && cfg.split_mode != PV_SPLIT_RECURSIVE) return PV_ERR_ARG;
+  if (cfg.profile_mode != PV_PROFILE_CUBIC && cfg.profile_mode != PV_PROFILE_TEMPLATE)
+    return PV_ERR_ARG;
   if (!(cfg.mv_chi2_cut > 0.0f) || !(cfg.mv_dz_tol >= 0.0f) || !(cfg.mv_w_assoc > 0.0f) ||
       !(cfg.mv_w_assoc <= 1.0f) || !(cfg.mv_dup_sep2 >= 0.0f))
     return PV_ERR_ARG;
@@ -291,6 +294,8 @@ int compute_consts(const pv_config& cfg, const pv_beamline& b, Consts* C) {
   C->mv_w_assoc = cfg.mv_w_assoc;
   C->mv_dup_sep2 = cfg.mv_dup_sep2;
   C->split_mode = cfg.split_mode;
+  C->profile_mode = cfg.profile_mode;
+  C->tpl = nullptr;
   C->thr = cfg.bin_threshold;
   C->t_pp = static_cast<uint32_t>(std::llround(static_cast<double>(cfg.min_integral_pp) * PV_ONE));
   C->t_gas = static_cast<uint32_t>(std::llround(static_cast<double>(cfg.min_integral_gas) * PV_ONE));
@@ -580,7 +585,7 @@ void pv_config_default(pv_config* c) {
   c->mv_w_assoc = 0.5f;
   c->mv_dup_sep2 = 25.0f;
   c->split_mode = PV_SPLIT_ZORDER;
-  c->reserved2 = 0;
+  c->profile_mode = PV_PROFILE_CUBIC;
 }
 
 int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** out) {
@@ -607,9 +612,30 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
     delete ctx;
     return PV_ERR_CUDA;
   }
+  if (C.profile_mode == PV_PROFILE_TEMPLATE) {
+    // the x86 profile's template table, built once on the device
+    int status = 1;
+    if (ctx->tpl.ensure(sizeof(pvdev::TplTable)) != cudaSuccess ||
+        pvk::build_template_table(static_cast<pvdev::TplTable*>(ctx->tpl.p), C.dz, 0) !=
+            cudaSuccess ||
+        cudaMemcpy(&status, &static_cast<pvdev::TplTable*>(ctx->tpl.p)->status, sizeof(int),
+                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+      ctx->tpl.release();
+      delete ctx;
+      return PV_ERR_CUDA;
+    }
+    if (status != 0) {            // bins too narrow for the widest template
+      ctx->tpl.release();
+      delete ctx;
+      return PV_ERR_ARG;
+    }
+    ctx->C.tpl = static_cast<const pvdev::TplTable*>(ctx->tpl.p);
+  }
   const int nts[4] = {64, 96, 128, 256};
+  const int flav = pvk::flavour_of(C);
   for (int mode = 1; mode <= 3; ++mode)
-    for (int i = 0; i < 4; ++i) ctx->find_per_sm[mode][i] = pvk::fused_blocks_per_sm(C.nbins, mode, nts[i]);
+    for (int i = 0; i < 4; ++i)
+      ctx->find_per_sm[mode][i] = pvk::fused_blocks_per_sm(C.nbins, mode, nts[i], flav);
   for (int k = 0; k < 3; ++k)
     for (int i = 0; i < 2; ++i) ctx->fit_per_sm[k][i] = pvk::fit_blocks_per_sm(k, i == 0 ? 128 : 256);
   for (int b = 0; b < 3; ++b) ctx->bucket_cfg[b] = pvk::LaunchCfg{128, 0, pvk::kFitThreads, 0};
@@ -649,6 +675,7 @@ int pv_destroy(pv_ctx* ctx) {
   ctx->fused_ws.release();
   ctx->plain_ws.release();
   ctx->mv_ws.release();
+  ctx->tpl.release();
   ctx->host_in.release();
   ctx->host_out.release();
   ctx->pool.release();

@@ -50,7 +50,41 @@ struct Consts {
   float mv_ecut;            // exp(-chi2_cut / 2)
   float mv_dz_tol, mv_w_assoc, mv_dup_sep2;
   int32_t split_mode;       // PV_SPLIT_*
+  int32_t profile_mode;     // PV_PROFILE_*
+  const struct TplTable* tpl;   // template profiles (device memory)
 };
+
+// ---------------------------------------------------------------------------
+// template profiles of the x86 flavour (Sec. 3.2): class k has
+// sigma_k = 0.01 mm 2^(k/4) and takes sigma_poca from sigma_{k-1} 2^(1/8) up.
+// q holds, per class, the quantised Gaussian CDF Q[0 .. 2H+1] at the bin
+// edges (i - H - 1/2) dz around the centre bin, Q[0] = 0, Q[2H+1] = ONE.
+constexpr int kTplClasses = 41;
+constexpr int kTplMaxHalf = 1024;
+constexpr int kTplCap = 16384;               // entries of q
+constexpr double kTplSigma0 = 0.01;          // mm
+constexpr double kTplRatio = 1.189207115002721;       // 2^(1/4)
+constexpr double kTplHalfRatio = 1.0905077326652577;  // 2^(1/8)
+
+struct TplTable {
+  double bound[kTplClasses];   // lowest sigma_poca of class k; bound[0] = 0
+  int32_t half[kTplClasses];   // H_k
+  int32_t first[kTplClasses];  // start of class k in q
+  int32_t status;              // 0 ok, 1 the table does not fit
+  int32_t q[kTplCap];
+};
+
+// class of sigma_poca: the last class whose lower bound it reaches
+__device__ __forceinline__ int tpl_class(float sigma, const TplTable* t) {
+  const double s = static_cast<double>(sigma);
+  int lo = 0, hi = kTplClasses - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s >= __ldg(t->bound + mid)) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 // ---------------------------------------------------------------------------
 // step (a): extrapolation, Eq. zpocadef, Eq. Vxy (diagonal block), sigma_poca
@@ -73,9 +107,13 @@ __device__ __forceinline__ float edge_of(int j, const Consts& C) {
 struct Prep {
   float zpoca, sigma;
   int center, j0, j1;
+  int tq;                  // template profile: start of its class in q
   bool filled;
 };
 
+// The profile window [j0, j1] is z_poca +- sqrt(5) sigma_poca for the cubic
+// profile and the class template's c - H .. c + H for kProfile = TEMPLATE.
+template <int kProfile = PV_PROFILE_CUBIC>
 __device__ __forceinline__ Prep prepare_track(float x, float y, float z, float tx, float ty,
                                               float cxx, float cxtx, float ctxtx,
                                               const Consts& C) {
@@ -97,18 +135,27 @@ __device__ __forceinline__ Prep prepare_track(float x, float y, float z, float t
   r.center = -1;
   r.j0 = 0;
   r.j1 = -1;
+  r.tq = 0;
   if (!(t2 > 0.0f)) return r;
   if (!isfinite(zp) || !isfinite(sig)) return r;
   int c = bin_of(zp, C);
   if (c < 0 || c >= C.nbins) return r;
   float smax = (zp < C.z_gas) ? C.sig_max_gas : C.sig_max_pp;
   if (!(sig <= smax)) return r;
-  float s = __fmul_rn(kSqrt5, sig);
-  if (s < kSMin) s = 0.0f;
   r.filled = true;
   r.center = c;
-  r.j0 = bin_of(__fsub_rn(zp, s), C);
-  r.j1 = bin_of(__fadd_rn(zp, s), C);
+  if constexpr (kProfile == PV_PROFILE_TEMPLATE) {
+    const int k = tpl_class(sig, C.tpl);
+    const int H = __ldg(C.tpl->half + k);
+    r.tq = __ldg(C.tpl->first + k);
+    r.j0 = c - H;
+    r.j1 = c + H;
+  } else {
+    float s = __fmul_rn(kSqrt5, sig);
+    if (s < kSMin) s = 0.0f;
+    r.j0 = bin_of(__fsub_rn(zp, s), C);
+    r.j1 = bin_of(__fadd_rn(zp, s), C);
+  }
   return r;
 }
 
@@ -151,6 +198,16 @@ __device__ __forceinline__ void fill_profile(uint32_t* hist, float zpoca, float 
   }
 }
 
+// Add one filled track's template profile (class start tq in q) to hist.
+__device__ __forceinline__ void fill_template(uint32_t* hist, int tq, int j0, int j1,
+                                              const Consts& C) {
+  const int32_t* q = C.tpl->q + tq;
+  for (int j = j0; j <= j1; ++j) {
+    const int w = __ldg(q + (j - j0) + 1) - __ldg(q + (j - j0));
+    if (w > 0 && j >= 0 && j < C.nbins) atomicAdd(hist + j, static_cast<uint32_t>(w));
+  }
+}
+
 // Warp-cooperative fill of the profiles of the 32 tracks held by the lanes
 // (one per lane; nb = 0 for a lane without a filled track).  The warp's
 // (track, bin) items are spread over the lanes, so no lane idles while
@@ -163,13 +220,20 @@ __device__ __forceinline__ void fill_profile(uint32_t* hist, float zpoca, float 
 // non-decreasing along a window because F is monotone on [-1, 1], every
 // binary32 step of u and F is a monotone rounding, and window edges are at
 // least dz / (sqrt(5) sigma_max) = 0.011 apart in u, far above the rounding
-// error of F.  The histogram is therefore the one fill_profile builds.
+// error of F.  The histogram is therefore the one fill_profile builds.  With
+// kProfile = TEMPLATE the left-edge value is the class template's Q[i] (tq:
+// the class's start in q) instead of the CDF, and the histogram is the one
+// fill_template builds.
+template <int kProfile = PV_PROFILE_CUBIC>
 __device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, float sigma,
-                                                   int j0, int nb, const Consts& C) {
+                                                   int j0, int nb, int tq, const Consts& C) {
   const int lane = threadIdx.x & 31;
-  float s = __fmul_rn(kSqrt5, sigma);
-  if (s < kSMin) s = 0.0f;
-  const float inv_s = (nb > 1 && s > 0.0f) ? __fdiv_rn(1.0f, s) : 0.0f;
+  float inv_s = 0.0f;
+  if constexpr (kProfile != PV_PROFILE_TEMPLATE) {
+    float s = __fmul_rn(kSqrt5, sigma);
+    if (s < kSMin) s = 0.0f;
+    inv_s = (nb > 1 && s > 0.0f) ? __fdiv_rn(1.0f, s) : 0.0f;
+  }
   int incl = nb;                      // inclusive prefix of the window sizes
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -188,12 +252,17 @@ __device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, 
     const int o_incl = __shfl_sync(0xffffffffu, incl, L);
     const int o_nb = __shfl_sync(0xffffffffu, nb, L);
     const int o_j0 = __shfl_sync(0xffffffffu, j0, L);
-    const float o_z = __shfl_sync(0xffffffffu, zpoca, L);
-    const float o_inv = __shfl_sync(0xffffffffu, inv_s, L);
     const int i = idx - (o_incl - o_nb);
     const int j = o_j0 + i;
     int ql = 0;                       // quantised CDF at the left edge of bin j
-    if (idx < total && i > 0) ql = quant_cdf(__fmul_rn(__fsub_rn(edge_of(j, C), o_z), o_inv));
+    if constexpr (kProfile == PV_PROFILE_TEMPLATE) {
+      const int o_tq = __shfl_sync(0xffffffffu, tq, L);
+      if (idx < total && i > 0) ql = __ldg(C.tpl->q + o_tq + i);
+    } else {
+      const float o_z = __shfl_sync(0xffffffffu, zpoca, L);
+      const float o_inv = __shfl_sync(0xffffffffu, inv_s, L);
+      if (idx < total && i > 0) ql = quant_cdf(__fmul_rn(__fsub_rn(edge_of(j, C), o_z), o_inv));
+    }
     const int qn = __shfl_down_sync(0xffffffffu, ql, 1);
     const int qr = (i == o_nb - 1) ? kOne : qn;
     const int w = qr - ql;

@@ -217,9 +217,11 @@ __device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tr
 //           position is left in the output row, which the fit overwrites.
 // kFit:     seeds and assignments from the caller, then fit inputs and work.
 
-template <int MODE, int NT, int SPLIT = PV_SPLIT_ZORDER>
+template <int MODE, int NT, int FLAV = 0>
 __global__ void __launch_bounds__(NT)
 find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
+  constexpr int SPLIT = flavour_split(FLAV);
+  constexpr int PROFILE = flavour_profile(FLAV);
   extern __shared__ __align__(16) unsigned char smem[];
   const Layout Lo = make_layout(C.nbins, MODE);
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem + Lo.hist);
@@ -282,10 +284,11 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
         p.zpoca = p.sigma = 0.0f;
         p.j0 = 0;
         p.j1 = -1;
+        p.tq = 0;
         if (t < n) {
           const int64_t i = b0 + t;
-          p = prepare_track(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i], T.cxtx[i],
-                            T.ctxtx[i], C);
+          p = prepare_track<PROFILE>(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i],
+                                     T.cxtx[i], T.ctxtx[i], C);
           center[t] = static_cast<int16_t>(p.filled ? p.center : -1);
         }
         if (p.filled) {
@@ -296,7 +299,8 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
             if (!(tmask[q >> 5] & bit)) atomicOr(tmask + (q >> 5), bit);
           }
         }
-        warp_fill_profiles(hist, p.zpoca, p.sigma, p.j0, p.filled ? p.j1 - p.j0 + 1 : 0, C);
+        warp_fill_profiles<PROFILE>(hist, p.zpoca, p.sigma, p.j0,
+                                    p.filled ? p.j1 - p.j0 + 1 : 0, p.tq, C);
       }
       if (tid == NT - 1) misc[(iter + 1) & 1] = e_next;
       __syncthreads();
@@ -863,22 +867,28 @@ int mv_blocks_per_sm(void) {
 // ---------------------------------------------------------------------------
 // launch plumbing: kernel instantiations by block size
 
-template <int MODE, int NT, int SPLIT>
-static cudaError_t setup_find_split(int nbins) {
-  cudaError_t err = cudaFuncSetAttribute(find_kernel<MODE, NT, SPLIT>,
+template <int MODE, int NT, int FLAV>
+static cudaError_t setup_find_flav(int nbins) {
+  cudaError_t err = cudaFuncSetAttribute(find_kernel<MODE, NT, FLAV>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)fused_smem_bytes(nbins, MODE));
   if (err != cudaSuccess) return err;
-  return cudaFuncSetAttribute(find_kernel<MODE, NT, SPLIT>,
+  return cudaFuncSetAttribute(find_kernel<MODE, NT, FLAV>,
                               cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
 }
 
+// The GPU flavour (FLAV 0) at every block size; the x86 flavours of the peak
+// search and the profile (FLAV 1-3) at kFlavThreads for the modes that find.
 template <int MODE, int NT>
 static cudaError_t setup_find(int nbins) {
-  cudaError_t err = setup_find_split<MODE, NT, PV_SPLIT_ZORDER>(nbins);
-  if (err != cudaSuccess) return err;
-  return setup_find_split<MODE, NT, PV_SPLIT_RECURSIVE>(nbins);
+  cudaError_t err = setup_find_flav<MODE, NT, 0>(nbins);
+  if constexpr (MODE != kFit && NT == kFlavThreads) {
+    if (err == cudaSuccess) err = setup_find_flav<MODE, NT, 1>(nbins);
+    if (err == cudaSuccess) err = setup_find_flav<MODE, NT, 2>(nbins);
+    if (err == cudaSuccess) err = setup_find_flav<MODE, NT, 3>(nbins);
+  }
+  return err;
 }
 
 template <int NT>
@@ -900,10 +910,10 @@ cudaError_t fused_setup(int nbins) {
 bool find_block_ok(int nt) { return nt == 64 || nt == 96 || nt == 128 || nt == 256; }
 bool fit_block_ok(int ft) { return ft == 128 || ft == 256; }
 
-template <int MODE, int NT>
+template <int MODE, int NT, int FLAV = 0>
 static int find_blocks(int nbins) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, find_kernel<MODE, NT>, NT,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, find_kernel<MODE, NT, FLAV>, NT,
                                                     fused_smem_bytes(nbins, MODE)) != cudaSuccess)
     return 0;
   return blocks;
@@ -916,7 +926,17 @@ static int find_blocks_nt(int nbins, int mode) {
   return find_blocks<kFindFit, NT>(nbins);
 }
 
-int fused_blocks_per_sm(int nbins, int mode, int nt) {
+template <int MODE>
+static int find_blocks_flav(int nbins, int flav) {
+  if (flav == 1) return find_blocks<MODE, kFlavThreads, 1>(nbins);
+  if (flav == 2) return find_blocks<MODE, kFlavThreads, 2>(nbins);
+  return find_blocks<MODE, kFlavThreads, 3>(nbins);
+}
+
+int fused_blocks_per_sm(int nbins, int mode, int nt, int flav) {
+  if (flav != 0 && mode != kFit)
+    return mode == kFind ? find_blocks_flav<kFind>(nbins, flav)
+                         : find_blocks_flav<kFindFit>(nbins, flav);
   if (nt == 64) return find_blocks_nt<64>(nbins, mode);
   if (nt == 96) return find_blocks_nt<96>(nbins, mode);
   if (nt == 256) return find_blocks_nt<256>(nbins, mode);
@@ -958,16 +978,23 @@ template <int MODE, int NT>
 static void launch_find_nt(int grid, size_t sm, cudaStream_t st, const Consts& C,
                            const TrackPtrs& T, const SeedPtrs& S, const OutPtrs& O,
                            const TrackScratch& ws) {
-  if (C.split_mode == PV_SPLIT_RECURSIVE)
-    find_kernel<MODE, NT, PV_SPLIT_RECURSIVE><<<grid, NT, sm, st>>>(C, T, S, O, ws);
-  else
-    find_kernel<MODE, NT, PV_SPLIT_ZORDER><<<grid, NT, sm, st>>>(C, T, S, O, ws);
+  find_kernel<MODE, NT><<<grid, NT, sm, st>>>(C, T, S, O, ws);
 }
 
 template <int MODE>
 static void launch_find(int nt, int grid, size_t sm, cudaStream_t st, const Consts& C,
                         const TrackPtrs& T, const SeedPtrs& S, const OutPtrs& O,
                         const TrackScratch& ws) {
+  if constexpr (MODE != kFit) {
+    const int flav = flavour_of(C);
+    if (flav != 0) {
+      constexpr int NF = kFlavThreads;
+      if (flav == 1) find_kernel<MODE, NF, 1><<<grid, NF, sm, st>>>(C, T, S, O, ws);
+      else if (flav == 2) find_kernel<MODE, NF, 2><<<grid, NF, sm, st>>>(C, T, S, O, ws);
+      else find_kernel<MODE, NF, 3><<<grid, NF, sm, st>>>(C, T, S, O, ws);
+      return;
+    }
+  }
   if (nt == 64) launch_find_nt<MODE, 64>(grid, sm, st, C, T, S, O, ws);
   else if (nt == 96) launch_find_nt<MODE, 96>(grid, sm, st, C, T, S, O, ws);
   else if (nt == 256) launch_find_nt<MODE, 256>(grid, sm, st, C, T, S, O, ws);
@@ -993,14 +1020,78 @@ cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const Se
 }
 
 // ---------------------------------------------------------------------------
+// template table of the x86 profile (Sec. 3.2): sigma_k, the class bounds,
+// the smallest H_k whose outer edge quantises to 0, and the quantised
+// Gaussian CDF at the edges (i - H - 1/2) dz, all in binary64 with
+// round-to-nearest intrinsics, quantised with ties to even.
+
+__device__ __forceinline__ long long tpl_quant(int i, int H, double dz, double s) {
+  const double x = __ddiv_rn(__dmul_rn(__dsub_rn(static_cast<double>(i - H), 0.5), dz), s);
+  const double phi = __dmul_rn(0.5, erfc(__dmul_rn(-x, 0.70710678118654752440)));
+  return __double2ll_rn(__dmul_rn(static_cast<double>(kOne), phi));
+}
+
+__global__ void __launch_bounds__(256) template_table_kernel(TplTable* t, double dz) {
+  __shared__ double sig[kTplClasses];
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    double s = kTplSigma0;
+    int total = 0;
+    ok = 1;
+    for (int k = 0; k < kTplClasses; ++k) {
+      if (k > 0) {
+        t->bound[k] = __dmul_rn(s, kTplHalfRatio);
+        s = __dmul_rn(s, kTplRatio);
+      } else {
+        t->bound[k] = 0.0;
+      }
+      sig[k] = s;
+      int H = 0;
+      while (H < kTplMaxHalf && tpl_quant(0, H, dz, s) != 0) ++H;
+      t->half[k] = H;
+      t->first[k] = total;
+      total += 2 * H + 2;
+    }
+    if (total > kTplCap) ok = 0;
+    t->status = ok ? 0 : 1;
+  }
+  __syncthreads();
+  if (!ok) return;
+  for (int k = 0; k < kTplClasses; ++k) {
+    const int H = t->half[k];
+    int32_t* q = t->q + t->first[k];
+    // the quantised CDF is non-decreasing in i (monotone Phi, monotone
+    // roundings); the running maximum of the definition is taken below
+    for (int i = threadIdx.x; i <= 2 * H + 1; i += blockDim.x) {
+      long long v;
+      if (i == 0) v = 0;
+      else if (i == 2 * H + 1) v = kOne;
+      else v = tpl_quant(i, H, dz, sig[k]);
+      q[i] = static_cast<int32_t>(v < 0 ? 0 : (v > kOne ? kOne : v));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 1; i <= 2 * H + 1; ++i)
+        if (q[i] < q[i - 1]) q[i] = q[i - 1];
+    __syncthreads();
+  }
+}
+
+cudaError_t build_template_table(TplTable* t, float dz, cudaStream_t st) {
+  template_table_kernel<<<1, 256, 0, st>>>(t, static_cast<double>(dz));
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // plain per-step kernels
 
+template <int PROFILE>
 __global__ void plain_extrapolate_kernel(Consts C, TrackPtrs T, float* zpoca, float* sigma,
                                          int32_t* center, int32_t* j0, int32_t* j1) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T.n_tracks;
        i += (int64_t)gridDim.x * blockDim.x) {
-    Prep p = prepare_track(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i], T.cxtx[i],
-                           T.ctxtx[i], C);
+    Prep p = prepare_track<PROFILE>(T.x[i], T.y[i], T.z[i], T.tx[i], T.ty[i], T.cxx[i],
+                                    T.cxtx[i], T.ctxtx[i], C);
     if (zpoca) zpoca[i] = p.zpoca;
     if (sigma) sigma[i] = p.sigma;
     if (center) center[i] = p.filled ? p.center : -1;
@@ -1016,8 +1107,13 @@ __global__ void plain_hist_kernel(Consts C, TrackPtrs T, const float* zpoca, con
   const int64_t b0 = T.off[e], b1 = T.off[e + 1];
   if (offsets_bad(b0, b1, T.n_tracks)) return;
   uint32_t* h = hist + static_cast<size_t>(e) * C.nbins;
-  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x)
-    if (center[i] >= 0) fill_profile(h, zpoca[i], sigma[i], j0[i], j1[i], C);
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    if (center[i] < 0) continue;
+    if (C.profile_mode == PV_PROFILE_TEMPLATE)
+      fill_template(h, __ldg(C.tpl->first + tpl_class(sigma[i], C.tpl)), j0[i], j1[i], C);
+    else
+      fill_profile(h, zpoca[i], sigma[i], j0[i], j1[i], C);
+  }
 }
 
 template <int SPLIT>
@@ -1145,8 +1241,9 @@ static int grid_for(int64_t n, int threads) {
 cudaError_t launch_extrapolate(const Consts& C, const TrackPtrs& T, float* zpoca, float* sigma,
                                int32_t* center, cudaStream_t st) {
   if (T.n_tracks == 0) return cudaSuccess;
-  plain_extrapolate_kernel<<<grid_for(T.n_tracks, 256), 256, 0, st>>>(C, T, zpoca, sigma, center,
-                                                                      nullptr, nullptr);
+  // z_poca, sigma_poca and the centre bin do not depend on the profile
+  plain_extrapolate_kernel<PV_PROFILE_CUBIC><<<grid_for(T.n_tracks, 256), 256, 0, st>>>(
+      C, T, zpoca, sigma, center, nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -1155,8 +1252,12 @@ cudaError_t launch_histogram(const Consts& C, const TrackPtrs& T, uint32_t* hist
   cudaError_t err = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)T.n_events * C.nbins, st);
   if (err != cudaSuccess) return err;
   if (T.n_tracks > 0) {
-    plain_extrapolate_kernel<<<grid_for(T.n_tracks, 256), 256, 0, st>>>(
-        C, T, ws.zpoca, ws.sigma, ws.center, ws.j0, ws.j1);
+    if (C.profile_mode == PV_PROFILE_TEMPLATE)
+      plain_extrapolate_kernel<PV_PROFILE_TEMPLATE><<<grid_for(T.n_tracks, 256), 256, 0, st>>>(
+          C, T, ws.zpoca, ws.sigma, ws.center, ws.j0, ws.j1);
+    else
+      plain_extrapolate_kernel<PV_PROFILE_CUBIC><<<grid_for(T.n_tracks, 256), 256, 0, st>>>(
+          C, T, ws.zpoca, ws.sigma, ws.center, ws.j0, ws.j1);
     ++*n_launches;
   }
   plain_hist_kernel<<<T.n_events, 256, 0, st>>>(C, T, ws.zpoca, ws.sigma, ws.center, ws.j0, ws.j1,

@@ -87,6 +87,25 @@ enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3 };
 constexpr int kSmallCap = 256;      // tracks kept in shared memory per event
 constexpr int kFusedThreads = 128;
 
+// Flavour of the find kernel: bit 0 the x86 recursive dip split, bit 1 the
+// x86 template profile.  The GPU flavour (0) is built for every block size,
+// the others for kFlavThreads.
+constexpr int kFlavThreads = 128;
+__host__ __device__ constexpr int flavour_split(int f) {
+  return (f & 1) ? PV_SPLIT_RECURSIVE : PV_SPLIT_ZORDER;
+}
+__host__ __device__ constexpr int flavour_profile(int f) {
+  return (f & 2) ? PV_PROFILE_TEMPLATE : PV_PROFILE_CUBIC;
+}
+inline int flavour_of(const pvdev::Consts& C) {
+  return (C.split_mode == PV_SPLIT_RECURSIVE ? 1 : 0) |
+         (C.profile_mode == PV_PROFILE_TEMPLATE ? 2 : 0);
+}
+
+// Fills the template table of the x86 profile for bin width dz (one small
+// kernel); t->status becomes 1 if the templates do not fit.
+cudaError_t build_template_table(pvdev::TplTable* t, float dz, cudaStream_t st);
+
 // Scratch of the plain per-step path.
 struct PlainScratch {
   float* zpoca;
@@ -125,7 +144,7 @@ cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, c
 
 bool find_block_ok(int nt);
 bool fit_block_ok(int ft);
-int fused_blocks_per_sm(int nbins, int mode, int nt);
+int fused_blocks_per_sm(int nbins, int mode, int nt, int flav);
 int fit_blocks_per_sm(int accum, int ft);
 constexpr int kFitThreads = 256;
 
@@ -144,9 +163,6 @@ inline long long class_capacity(int c, long long n_tracks, long long n_events, i
   long long by_tracks = n_tracks / kClassMinTracks[c];
   return by_tracks < all ? by_tracks : all;
 }
-
-int fused_blocks_per_sm(int nbins, int mode);
-int fit_blocks_per_sm(bool kahan);
 
 // Multi-vertex fit (GPU flavour of Sec. 3.5) of the seeds S into O.
 struct MvLastState {        // the sheared position a vertex's last weights were taken at

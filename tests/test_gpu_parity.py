@@ -303,3 +303,69 @@ def test_recursive_split_flavour(pv, path):
         fit = oracle.fit_batch(batch, ref, p)
         G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref, **cfg),
                            cond=(batch, ref, p))
+
+
+def _sigma_ladder_events():
+    """Events whose tracks' sigma_poca runs through every template class (log-
+    uniform from 5 um to 9.5 mm, p-gas region) and, capped at 1.5 mm, the pp
+    region; also tracks near both ends of the histogram."""
+    rng = np.random.default_rng(17)
+    ev = []
+    for z0, smax in ((-420.0, 9.5), (0.0, 1.45), (-549.8, 9.5), (299.7, 1.45)):
+        n = 120
+        sig = np.exp(rng.uniform(np.log(0.005), np.log(smax), n))
+        t = rng.uniform(0.05, 0.3, (n, 2)) * rng.choice([-1.0, 1.0], (n, 2))
+        tt = np.sqrt((t ** 2).sum(axis=1))
+        e = synthetic.straight_tracks((0.0, 0.0, z0), t, z0 + rng.uniform(-1.0, 1.0, n),
+                                      cov_xx=1.0, cov_tt=1e-12)
+        e["cxx"] = ((sig * tt) ** 2).astype(np.float32)
+        e["cyy"] = e["cxx"].copy()
+        ev.append(e)
+    return synthetic.batch_from_events(ev)
+
+
+def test_template_profile_histogram_bit_exact(pv):
+    """The x86 profile (Sec. 3.2, reading R17): the device's template table
+    (built with the device's erfc) and fill give the oracle's histograms bit
+    for bit, for sigma_poca in every template class and at the range ends."""
+    import torch
+    batch = _sigma_ladder_events()
+    p = oracle.default_params(profile_mode=1)
+    prep = oracle.prepare_f32(batch.tracks, p)
+    tpl = oracle.template_table(p)
+    classes = {int(np.searchsorted(tpl["bound"], s, side="right") - 1)
+               for s, f in zip(prep["sigma"], prep["filled"]) if f}
+    assert len(classes) == len(tpl["sigma"])
+    ctx = pv.Context(device=0, profile_mode=pv.PROFILE_TEMPLATE)
+    h = ctx.histogram_batch(pv.Tracks.from_batch(batch))
+    torch.cuda.synchronize()
+    ctx.close()
+    ref = oracle.find_batch(batch, p, want_hist=True)
+    assert np.array_equal(h.cpu().numpy().view(np.uint32), ref["hist"])
+    # the events through the fused find (its own fill) against the oracle
+    ctx = pv.Context(device=0, profile_mode=pv.PROFILE_TEMPLATE)
+    s, v = G.gpu_find_fit(ctx, batch)
+    ctx.close()
+    G.assert_find_equal(s, oracle.find_batch(batch, p), batch)
+
+
+@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_template_profile_flavour(pv, path, split):
+    """The x86 profile alone and with the x86 split (the full x86 flavour of
+    steps b and c) through both paths: seeds bit-exact and the fit within
+    tolerance on the nominal workload and the pp + p-gas overlay."""
+    cfg = dict(profile_mode=pv.PROFILE_TEMPLATE, split_mode=split)
+    if path == "plain":
+        cfg["path"] = pv.PATH_PLAIN
+    for batch in (synthetic.workload_nominal(n_events=1500, seed=15),
+                  synthetic.workload_overlay(n_events=800, seed=16)):
+        ctx = pv.Context(device=0, **cfg)
+        s, v = G.gpu_find_fit(ctx, batch)
+        ctx.close()
+        p = oracle.default_params(profile_mode=1, split_mode=split)
+        ref = oracle.find_batch(batch, p)
+        G.assert_find_equal(s, ref, batch)
+        fit = oracle.fit_batch(batch, ref, p)
+        G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref, **cfg),
+                           cond=(batch, ref, p))
