@@ -530,6 +530,16 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": launches,
     }
+    # physics figures of merit (Sec. 4) of the timed outputs on the synthetic truth
+    from paper_2412_14966_gb300 import physics
+    vo = outs[0].numpy()
+    ph = physics.evaluate(batch, vo["x"][:E], vo["y"][:E], vo["z"][:E], vo["cov"][:E],
+                          vo["status"][:E], vo["n_per_event"][:E], vo["n_tracks"][:E])
+    line["physics"] = {k: ph[k] for k in ("efficiency", "efficiency_isolated", "efficiency_close",
+                                          "fake_rate", "reconstructible", "matched")}
+    if ph["pp"]:
+        line["physics"]["resolution_um"] = ph["pp"]["resolution_um"]
+        line["physics"]["pull_width"] = ph["pp"]["pull_width"]
     if args.serve_rate > 0:
         line["serving"] = serving_run(pv, ctx, args.serve_rate)
     if rank == 0 and world == 1:
