@@ -345,21 +345,26 @@ __host__ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t to
 // than its neighbours inside [a, b]; equal maxima by lower position; leftmost
 // minimum), split there when the dip is significant against the smaller
 // maximum and both sides hold the minimal integral, then the same on each
-// side.  Calls emit(lo, hi, integral, im) per piece in z order.  Pieces come
-// out in z order, so a pending right-hand side starts one bin after the last
-// piece emitted and only its last bin waits on the stack.  The stack holds
-// kRecDepth entries; a deeper nesting (each pending side holds at least the
-// smaller minimal integral, so it needs a proto-cluster of more than
-// kRecDepth x 1.75 tracks' weight arranged as a nested comb) emits the
-// remaining range whole.
+// side.  Calls emit(lo, hi, integral, im) per piece in z order; total is the
+// integral of [a, b].  A range's first-found largest maximum is its argmax
+// (lowest index), and a side's integral is the parent's minus the other
+// side's, so a range costs one scan for its maxima plus the sum of its left
+// side.  Pieces come out in z order, so a pending right-hand side starts one
+// bin after the last piece emitted and only its last bin and integral wait on
+// the stack.  The stack holds kRecDepth entries; a deeper nesting (each
+// pending side holds at least the smaller minimal integral, so it needs a
+// proto-cluster of more than kRecDepth x 1.75 tracks' weight arranged as a
+// nested comb) emits the remaining range whole.
 constexpr int kRecDepth = 256;
 
 template <class Emit>
-__host__ __device__ void split_recursive(const uint32_t* N, int a, int b, const Consts& C,
-                                         Emit&& emit) {
+__host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64_t total,
+                                         const Consts& C, Emit&& emit) {
   int16_t st_hi[kRecDepth];
+  uint64_t st_int[kRecDepth];
   int sp = 0;
   int lo = a, hi = b;
+  uint64_t integral = total;
   for (;;) {
     int m1 = -1, m2 = -1;
     for (int i = lo; i <= hi;) {
@@ -377,37 +382,34 @@ __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, const 
       }
       i = q + 1;
     }
-    bool split = false;
-    int m = -1;
     if (m2 >= 0 && sp < kRecDepth) {
       const int l = m1 < m2 ? m1 : m2, h = m1 < m2 ? m2 : m1;
+      int m = -1;
       for (int i = l + 1; i < h; ++i)
         if (m < 0 || N[i] < N[m]) m = i;
       const uint32_t lower = N[m1] < N[m2] ? N[m1] : N[m2];
       if (m >= 0 &&
           static_cast<uint64_t>(C.dip_den) * N[m] < static_cast<uint64_t>(C.dip_num) * lower) {
         const uint64_t T = (m < C.gas_bin) ? C.t_gas : C.t_pp;
-        uint64_t left = 0, right = 0;
+        uint64_t left = 0;
         for (int i = lo; i <= m; ++i) left += N[i];
-        for (int i = m + 1; i <= hi; ++i) right += N[i];
-        split = left >= T && right >= T;
+        const uint64_t right = integral - left;
+        if (left >= T && right >= T) {
+          st_hi[sp] = static_cast<int16_t>(hi);
+          st_int[sp] = right;
+          ++sp;
+          hi = m;
+          integral = left;
+          continue;
+        }
       }
     }
-    if (split) {
-      st_hi[sp++] = static_cast<int16_t>(hi);
-      hi = m;
-      continue;
-    }
-    uint64_t integral = 0;
-    int im = lo;
-    for (int i = lo; i <= hi; ++i) {
-      integral += N[i];
-      if (N[i] > N[im]) im = i;
-    }
-    emit(lo, hi, integral, im);
+    emit(lo, hi, integral, m1);
     if (sp == 0) break;
+    --sp;
     lo = hi + 1;
-    hi = st_hi[--sp];
+    hi = st_hi[sp];
+    integral = st_int[sp];
   }
 }
 
@@ -416,7 +418,7 @@ template <int kSplit, class Emit>
 __host__ __device__ __forceinline__ void split_pieces(const uint32_t* N, int a, int b,
                                                       uint64_t total, const Consts& C,
                                                       Emit&& emit) {
-  if constexpr (kSplit == PV_SPLIT_RECURSIVE) split_recursive(N, a, b, C, emit);
+  if constexpr (kSplit == PV_SPLIT_RECURSIVE) split_recursive(N, a, b, total, C, emit);
   else split_walk(N, a, b, total, C, emit);
 }
 
