@@ -125,10 +125,11 @@ def test_default_config_is_the_papers(lib):
     p = oracle.default_params()
     assert (c.bin_threshold, c.dip_num, c.dip_den) == (p.bin_threshold, p.dip_num, p.dip_den)
     assert c.split_mode == p.split_mode == pv.SPLIT_ZORDER
+    assert c.profile_mode == p.profile_mode == pv.PROFILE_CUBIC
 
 
-@pytest.mark.parametrize("field,value", [("split_mode", 2), ("split_mode", -1), ("dz", 0.0),
-                                         ("mv_chi2_cut", 0.0)])
+@pytest.mark.parametrize("field,value", [("split_mode", 2), ("split_mode", -1),
+                                         ("profile_mode", 2), ("dz", 0.0), ("mv_chi2_cut", 0.0)])
 def test_invalid_config_is_refused_before_the_device(lib, field, value):
     """pv_init checks the configuration before it looks for a device."""
     import paper_2412_14966_gb300 as pv
