@@ -739,7 +739,7 @@ int pv_fit_multi(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
   size_t o = 0;
   const size_t o_cnt = o; o += 256;
   const size_t o_K = o; o += round16(sizeof(int) * E);
-  const size_t o_S = o; o += round16(sizeof(float) * n);
+  const size_t o_P = o; o += round16(3 * sizeof(float4) * n);
   const size_t o_work = o; o += round16(sizeof(int2) * slots);
   const size_t o_sx = o; o += round16(sizeof(float) * slots);
   const size_t o_sy = o; o += round16(sizeof(float) * slots);
@@ -754,7 +754,7 @@ int pv_fit_multi(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
   pvk::MvScratch M;
   M.counters = reinterpret_cast<int*>(base + o_cnt);
   M.K = reinterpret_cast<int*>(base + o_K);
-  M.S = reinterpret_cast<float*>(base + o_S);
+  M.P = reinterpret_cast<float4*>(base + o_P);
   M.work = reinterpret_cast<int2*>(base + o_work);
   M.sx = reinterpret_cast<float*>(base + o_sx);
   M.sy = reinterpret_cast<float*>(base + o_sy);

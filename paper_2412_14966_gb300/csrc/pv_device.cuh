@@ -366,30 +366,43 @@ __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64
   int lo = a, hi = b;
   uint64_t integral = total;
   for (;;) {
+    // one pass over the runs of equal bins (one load per bin): a run is a
+    // maximum if the bins on both sides are lower (the range ends count as
+    // lower); runs come in z order, so equal maxima keep the lower position
     int m1 = -1, m2 = -1;
-    for (int i = lo; i <= hi;) {
-      int q = i;
-      while (q < hi && N[q + 1] == N[i]) ++q;
-      const bool left_lower = i == lo || N[i - 1] < N[i];
-      const bool right_lower = q == hi || N[q + 1] < N[i];
-      if (left_lower && right_lower) {
-        if (m1 < 0 || N[i] > N[m1]) {
-          m2 = m1;
-          m1 = i;
-        } else if (m2 < 0 || N[i] > N[m2]) {
-          m2 = i;
+    uint32_t v1 = 0, v2 = 0;
+    {
+      int start = lo;
+      uint32_t v = N[lo];
+      bool left_lower = true;
+      for (int i = lo + 1; i <= hi + 1; ++i) {
+        const uint32_t nv = i <= hi ? N[i] : 0u;
+        if (i > hi || nv != v) {
+          if (left_lower && (i > hi || nv < v)) {
+            if (m1 < 0 || v > v1) {
+              m2 = m1; v2 = v1;
+              m1 = start; v1 = v;
+            } else if (m2 < 0 || v > v2) {
+              m2 = start; v2 = v;
+            }
+          }
+          left_lower = v < nv;
+          start = i;
+          v = nv;
         }
       }
-      i = q + 1;
     }
     if (m2 >= 0 && sp < kRecDepth) {
       const int l = m1 < m2 ? m1 : m2, h = m1 < m2 ? m2 : m1;
       int m = -1;
-      for (int i = l + 1; i < h; ++i)
-        if (m < 0 || N[i] < N[m]) m = i;
-      const uint32_t lower = N[m1] < N[m2] ? N[m1] : N[m2];
+      uint32_t vm = 0;
+      for (int i = l + 1; i < h; ++i) {
+        const uint32_t x = N[i];
+        if (m < 0 || x < vm) { m = i; vm = x; }
+      }
+      const uint32_t lower = v1 < v2 ? v1 : v2;
       if (m >= 0 &&
-          static_cast<uint64_t>(C.dip_den) * N[m] < static_cast<uint64_t>(C.dip_num) * lower) {
+          static_cast<uint64_t>(C.dip_den) * vm < static_cast<uint64_t>(C.dip_num) * lower) {
         const uint64_t T = (m < C.gas_bin) ? C.t_gas : C.t_pp;
         uint64_t left = 0;
         for (int i = lo; i <= m; ++i) left += N[i];

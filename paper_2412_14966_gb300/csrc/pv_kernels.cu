@@ -529,15 +529,16 @@ __device__ __forceinline__ float mv_seed_term(float X, float Y, float wx, float 
   return __expf(-0.5f * (X * X * wx + Y * Y * wy));
 }
 
-__device__ __forceinline__ bool mv_track(const TrackPtrs& T, int64_t t, float xs, float ys,
-                                         float zs, float S, MvTrack* m) {
+// p: the track's packed record (three float4, written by mv_seed_kernel).
+__device__ __forceinline__ bool mv_track(const float4* p, float xs, float ys, float zs,
+                                         MvTrack* m) {
+  const float4 a = p[0], b = p[1], c4 = p[2];
   float4 A;
   float2 W;
-  make_fit_track(T.x[t], T.y[t], T.z[t], T.tx[t], T.ty[t], T.cxx[t], T.cxtx[t], T.ctxtx[t],
-                 T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, &A, &W);
+  make_fit_track(a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c4.x, c4.y, c4.z, xs, ys, zs, &A, &W);
   if (!(W.x > 0.0f)) return false;
   m->X = A.x; m->Y = A.y; m->tx = A.z; m->ty = A.w; m->wx = W.x; m->wy = W.y;
-  const float c = S - mv_seed_term(A.x, A.y, W.x, W.y);
+  const float c = c4.w - mv_seed_term(A.x, A.y, W.x, W.y);
   m->comp = c > 0.0f ? c : 0.0f;
   return true;
 }
@@ -558,20 +559,18 @@ __device__ __forceinline__ float mv_chi2_at(const MvTrack& m, const MvLast& L) {
 }
 
 // Multi-vertex fit of one vertex per 8-lane group (binary32 sums), over all n
-// tracks of the event starting at global index b0 (lane r of the group takes
-// every 8th); S[s] is track s's seed sum.  Same normal equations, shear and
-// solve as group_fit; the stop rule is |dz| < mv_dz_tol alone and a track
-// counts for the vertex from weight mv_w_assoc on.  Every lane of the warp
-// must call it.
-__device__ void group_fit_multi(const TrackPtrs& T, int64_t b0, int n, const float* S,
-                                float xs, float ys, float zs, bool active, const Consts& C,
-                                VertexOut* out, MvLast* last) {
+// tracks of the event whose packed records start at rec (lane r of the group
+// takes every 8th).  Same normal equations, shear and solve as group_fit; the
+// stop rule is |dz| < mv_dz_tol alone and a track counts for the vertex from
+// weight mv_w_assoc on.  Every lane of the warp must call it.
+__device__ void group_fit_multi(const float4* rec, int n, float xs, float ys, float zs,
+                                bool active, const Consts& C, VertexOut* out, MvLast* last) {
   const int r = threadIdx.x & (kGroup - 1);
   const int cnt = active ? n : 0;
   float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
   for (int s = r; s < cnt; s += kGroup) {
     MvTrack m;
-    if (!mv_track(T, b0 + s, xs, ys, zs, S[s], &m)) continue;
+    if (!mv_track(rec + 3 * s, xs, ys, zs, &m)) continue;
     m0 += m.wx; m1 += m.wx * m.tx; m2 += m.wy; m3 += m.wy * m.ty;
   }
   m0 = group_sum(m0); m1 = group_sum(m1); m2 = group_sum(m2); m3 = group_sum(m3);
@@ -592,7 +591,7 @@ __device__ void group_fit_multi(const TrackPtrs& T, int64_t b0, int n, const flo
     if (!done) {
       for (int s = r; s < cnt; s += kGroup) {
         MvTrack m;
-        if (!mv_track(T, b0 + s, xs, ys, zs, S[s], &m)) continue;
+        if (!mv_track(rec + 3 * s, xs, ys, zs, &m)) continue;
         const float dtx = m.tx - P.cx, dty = m.ty - P.cy;
         const float rx = m.X + P.az * dtx - P.axp;
         const float ry = m.Y + P.az * dty - P.ayp;
@@ -674,8 +673,9 @@ __device__ void group_fit_multi(const TrackPtrs& T, int64_t b0, int n, const flo
 }
 
 // The multi-vertex fit runs as three kernels:
-//   mv_seed_kernel   one warp per event: each track's seed sum S (global) and
-//                    one work item (event, vertex) per seed;
+//   mv_seed_kernel   one warp per event: each track's packed record with its
+//                    seed sum S (global) and one work item (event, vertex) per
+//                    seed;
 //   mv_fit_kernel    persistent, four vertices per warp from the work list,
 //                    any event: the fits (group_fit_multi);
 //   mv_final_kernel  one warp per event: each track's vertex from the last-
@@ -738,7 +738,12 @@ mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
       make_fit_track(x, y, z, tx, ty, a, b, c, d, f, g, kx, ky, kz, &A, &W);
       if (W.x > 0.0f) sum += mv_seed_term(A.x, A.y, W.x, W.y);
     }
-    if (valid) M.S[i] = sum;
+    if (valid) {
+      float4* q = M.P + 3 * i;
+      q[0] = make_float4(x, y, z, tx);
+      q[1] = make_float4(ty, a, b, c);
+      q[2] = make_float4(d, f, g, sum);
+    }
   }
   // work items: one per seed
   int wb = 0;
@@ -776,7 +781,7 @@ mv_fit_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
     const float zs = has ? M.sz[slot] : 0.f;
     VertexOut out;
     MvLast L;
-    group_fit_multi(T, b0, n, M.S + b0, xs, ys, zs, has, C, &out, &L);
+    group_fit_multi(M.P + 3 * b0, n, xs, ys, zs, has, C, &out, &L);
     if (has && r == 0) {
       const size_t q = static_cast<size_t>(e) * O.cap + k;
       O.x[q] = xs + out.x;
@@ -817,7 +822,7 @@ mv_final_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
     for (int j = 0; j < K; ++j) {
       if (M.vst[s0 + j] & PV_ST_SINGULAR) continue;
       MvTrack m;
-      if (!mv_track(T, b0 + t, M.sx[s0 + j], M.sy[s0 + j], M.sz[s0 + j], M.S[b0 + t], &m))
+      if (!mv_track(M.P + 3 * (b0 + t), M.sx[s0 + j], M.sy[s0 + j], M.sz[s0 + j], &m))
         continue;
       const float w = mv_weight(mv_chi2_at(m, M.last[s0 + j]), m.comp, C);
       if (w > wbest) {

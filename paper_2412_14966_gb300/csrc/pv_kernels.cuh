@@ -171,7 +171,8 @@ struct MvLastState {        // the sheared position a vertex's last weights were
 struct MvScratch {
   int* counters;            // [0] work items listed, [1] next item to fit
   int* K;                   // per event: seeds fitted
-  float* S;                 // per track: sum over the event's seeds of exp(-chi2/2)
+  float4* P;                // per track, three float4: x y z tx | ty cxx cxtx ctxtx |
+                            // cyy cyty ctyty S, S = sum over the event's seeds of exp(-chi2/2)
   int2* work;               // (event, seed) per vertex
   float *sx, *sy, *sz;      // per slot [event][kMaxSeeds]: seed position
   MvLastState* last;        // per slot: last-iteration state
