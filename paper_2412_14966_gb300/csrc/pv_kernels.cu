@@ -502,7 +502,21 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
       W = G.W + w.off + r;
       stride = kGroup;
     }
-    for (int s = r, q = 0; s < cntk; s += kGroup, q += stride) {
+    // two tracks per pass: both tracks' loads are in flight together
+    int s = r, q = 0;
+    for (; s + kGroup < cntk; s += 2 * kGroup, q += 2 * stride) {
+      const int t0 = G.sorted[w.off + s], t1 = G.sorted[w.off + s + kGroup];
+      const float a0 = T.x[t0], a1 = T.y[t0], a2 = T.z[t0], a3 = T.tx[t0], a4 = T.ty[t0];
+      const float a5 = T.cxx[t0], a6 = T.cxtx[t0], a7 = T.ctxtx[t0], a8 = T.cyy[t0];
+      const float a9 = T.cyty[t0], a10 = T.ctyty[t0];
+      const float b0 = T.x[t1], b1 = T.y[t1], b2 = T.z[t1], b3 = T.tx[t1], b4 = T.ty[t1];
+      const float b5 = T.cxx[t1], b6 = T.cxtx[t1], b7 = T.ctxtx[t1], b8 = T.cyy[t1];
+      const float b9 = T.cyty[t1], b10 = T.ctyty[t1];
+      make_fit_track(a0, a1, a2, a3, a4, a5, a6, a7, a8, a9, a10, xs, ys, zs, A + q, W + q);
+      make_fit_track(b0, b1, b2, b3, b4, b5, b6, b7, b8, b9, b10, xs, ys, zs, A + q + stride,
+                     W + q + stride);
+    }
+    if (s < cntk) {
       const int t = G.sorted[w.off + s];
       make_fit_track(T.x[t], T.y[t], T.z[t], T.tx[t], T.ty[t], T.cxx[t], T.cxtx[t], T.ctxtx[t],
                      T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, A + q, W + q);
@@ -1050,49 +1064,59 @@ __device__ __forceinline__ long long tpl_quant(int i, int H, double dz, double s
   return __double2ll_rn(__dmul_rn(static_cast<double>(kOne), phi));
 }
 
+// One thread per class finds sigma_k, its bound and H_k (sigma_k and the bound
+// by the same chain of products as a sequential loop); thread 0 lays the
+// classes out; all threads fill the quantised CDF values; thread k takes the
+// running maximum over class k.
 __global__ void __launch_bounds__(256) template_table_kernel(TplTable* t, double dz) {
   __shared__ double sig[kTplClasses];
+  __shared__ int first[kTplClasses + 1];
   __shared__ int ok;
-  if (threadIdx.x == 0) {
-    double s = kTplSigma0;
-    int total = 0;
-    ok = 1;
-    for (int k = 0; k < kTplClasses; ++k) {
-      if (k > 0) {
-        t->bound[k] = __dmul_rn(s, kTplHalfRatio);
-        s = __dmul_rn(s, kTplRatio);
-      } else {
-        t->bound[k] = 0.0;
-      }
-      sig[k] = s;
-      int H = 0;
-      while (H < kTplMaxHalf && tpl_quant(0, H, dz, s) != 0) ++H;
-      t->half[k] = H;
-      t->first[k] = total;
-      total += 2 * H + 2;
+  const int k = threadIdx.x;
+  if (k < kTplClasses) {
+    double s = kTplSigma0, bound = 0.0;
+    for (int j = 1; j <= k; ++j) {
+      bound = __dmul_rn(s, kTplHalfRatio);
+      s = __dmul_rn(s, kTplRatio);
     }
-    if (total > kTplCap) ok = 0;
+    t->bound[k] = bound;
+    sig[k] = s;
+    int H = 0;
+    while (H < kTplMaxHalf && tpl_quant(0, H, dz, s) != 0) ++H;
+    t->half[k] = H;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int total = 0;
+    for (int c = 0; c < kTplClasses; ++c) {
+      first[c] = total;
+      t->first[c] = total;
+      total += 2 * t->half[c] + 2;
+    }
+    first[kTplClasses] = total;
+    ok = total <= kTplCap;
     t->status = ok ? 0 : 1;
   }
   __syncthreads();
   if (!ok) return;
-  for (int k = 0; k < kTplClasses; ++k) {
-    const int H = t->half[k];
-    int32_t* q = t->q + t->first[k];
-    // the quantised CDF is non-decreasing in i (monotone Phi, monotone
-    // roundings); the running maximum of the definition is taken below
-    for (int i = threadIdx.x; i <= 2 * H + 1; i += blockDim.x) {
-      long long v;
-      if (i == 0) v = 0;
-      else if (i == 2 * H + 1) v = kOne;
-      else v = tpl_quant(i, H, dz, sig[k]);
-      q[i] = static_cast<int32_t>(v < 0 ? 0 : (v > kOne ? kOne : v));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-      for (int i = 1; i <= 2 * H + 1; ++i)
-        if (q[i] < q[i - 1]) q[i] = q[i - 1];
-    __syncthreads();
+  for (int idx = threadIdx.x; idx < first[kTplClasses]; idx += blockDim.x) {
+    int c = 0;
+    while (first[c + 1] <= idx) ++c;
+    const int H = t->half[c];
+    const int i = idx - first[c];
+    long long v;
+    if (i == 0) v = 0;
+    else if (i == 2 * H + 1) v = kOne;
+    else v = tpl_quant(i, H, dz, sig[c]);
+    t->q[idx] = static_cast<int32_t>(v < 0 ? 0 : (v > kOne ? kOne : v));
+  }
+  __syncthreads();
+  // the quantised CDF is non-decreasing in i (monotone Phi, monotone
+  // roundings); the running maximum of the definition is taken anyway
+  if (k < kTplClasses) {
+    int32_t* q = t->q + first[k];
+    for (int i = 1; i <= 2 * t->half[k] + 1; ++i)
+      if (q[i] < q[i - 1]) q[i] = q[i - 1];
   }
 }
 
