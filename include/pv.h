@@ -206,6 +206,16 @@ int pv_histogram_batch(pv_ctx* ctx, const pv_tracks* tracks, uint32_t* hist, voi
 /* Number of histogram bins of the context's configuration. */
 int pv_num_bins(const pv_ctx* ctx);
 
+/* Bounds-check record of the checked build (the library compiled with
+ * PV_CHECKED=1, a test build): its kernels test the indices of their main
+ * shared- and global-memory accesses and skip, and count, any that would leave
+ * its buffer.  Synchronises the current device, writes the number of such
+ * indices since the last call to *count and the code of the first one to
+ * *first_code (both 0 when none), and resets them.  Returns PV_OK in the
+ * checked build; the default build has no checks, writes 0 to both and returns
+ * PV_ERR_ARG (also for NULL arguments). */
+int pv_check_report(uint32_t* count, uint32_t* first_code);
+
 /* The whole method through host memory: copies the host SoA tracks to
  * context-owned device buffers, runs the fused find+fit, copies the vertex
  * outputs back into the host pv_vertices and synchronises cuda_stream.  All

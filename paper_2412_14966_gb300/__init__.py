@@ -36,7 +36,7 @@ EXPORTED = (
     "pv_extrapolate_batch", "pv_histogram_batch", "pv_num_bins", "pv_run_host", "pv_submit",
     "pv_poll", "pv_request_latency_ns", "pv_strerror", "pv_last_cuda_error", "pv_launch_count",
     "pv_find_fit_static", "pv_autotune", "pv_launch_config", "pv_set_launch_config",
-    "pv_fit_multi",
+    "pv_fit_multi", "pv_check_report",
 )
 
 
@@ -118,6 +118,7 @@ def load():
                                        C.c_void_p, C.c_void_p]
     L.pv_histogram_batch.argtypes = [C.c_void_p, P(pv_tracks), C.c_void_p, C.c_void_p]
     L.pv_num_bins.argtypes = [C.c_void_p]
+    L.pv_check_report.argtypes = [P(C.c_uint32), P(C.c_uint32)]
     L.pv_run_host.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
     L.pv_submit.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), P(C.c_uint64)]
     L.pv_poll.argtypes = [C.c_void_p, C.c_uint64, P(C.c_int)]
@@ -253,6 +254,13 @@ class Vertices:
 
     def numpy(self) -> dict:
         return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in self.a.items()}
+
+
+def check_report() -> tuple:
+    """``pv_check_report``: (checked build?, out-of-bounds count, first code)."""
+    n, first = C.c_uint32(0), C.c_uint32(0)
+    rc = load().pv_check_report(C.byref(n), C.byref(first))
+    return rc == PV_OK, int(n.value), int(first.value)
 
 
 class Context:

@@ -686,6 +686,15 @@ int pv_destroy(pv_ctx* ctx) {
 
 int pv_num_bins(const pv_ctx* ctx) { return ctx ? ctx->C.nbins : 0; }
 
+int pv_check_report(uint32_t* count, uint32_t* first_code) {
+  if (!count || !first_code) return PV_ERR_ARG;
+  unsigned c = 0, f = 0;
+  const bool checked = pvk::check_report(&c, &f);
+  *count = c;
+  *first_code = f;
+  return checked ? PV_OK : PV_ERR_ARG;
+}
+
 int pv_find_batch(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* seeds_out, void* stream) {
   if (!ctx) return PV_ERR_ARG;
   int rc = check_tracks(tracks);

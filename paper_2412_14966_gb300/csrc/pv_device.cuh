@@ -17,6 +17,20 @@
 
 namespace pvdev {
 
+// Checked build (compiled with PV_CHECKED=1 into a separate library for the
+// tests): the kernels test the indices of their main shared- and global-memory
+// accesses, skip an access that would leave its buffer and count it (read back
+// through pv_check_report).  The default build compiles the tests away.
+#ifndef PV_CHECKED
+#define PV_CHECKED 0
+#endif
+#if PV_CHECKED && defined(__CUDA_ARCH__)
+__device__ void check_failed(unsigned code);
+#define PV_CHECK(cond, code) ((cond) ? true : (::pvdev::check_failed(code), false))
+#else
+#define PV_CHECK(cond, code) true
+#endif
+
 constexpr int kOne = PV_ONE;
 constexpr int kMaxSeeds = PV_MAX_SEEDS;
 constexpr int kMaxBins = PV_MAX_BINS;
@@ -202,6 +216,7 @@ __device__ __forceinline__ void fill_profile(uint32_t* hist, float zpoca, float 
 __device__ __forceinline__ void fill_template(uint32_t* hist, int tq, int j0, int j1,
                                               const Consts& C) {
   const int32_t* q = C.tpl->q + tq;
+  if (!PV_CHECK(tq >= 0 && tq + (j1 - j0) + 1 < kTplCap, 3)) return;
   for (int j = j0; j <= j1; ++j) {
     const int w = __ldg(q + (j - j0) + 1) - __ldg(q + (j - j0));
     if (w > 0 && j >= 0 && j < C.nbins) atomicAdd(hist + j, static_cast<uint32_t>(w));
@@ -257,7 +272,7 @@ __device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, 
     int ql = 0;                       // quantised CDF at the left edge of bin j
     if constexpr (kProfile == PV_PROFILE_TEMPLATE) {
       const int o_tq = __shfl_sync(0xffffffffu, tq, L);
-      if (idx < total && i > 0) ql = __ldg(C.tpl->q + o_tq + i);
+      if (idx < total && i > 0 && PV_CHECK(o_tq + i < kTplCap, 1)) ql = __ldg(C.tpl->q + o_tq + i);
     } else {
       const float o_z = __shfl_sync(0xffffffffu, zpoca, L);
       const float o_inv = __shfl_sync(0xffffffffu, inv_s, L);
@@ -266,7 +281,8 @@ __device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, 
     const int qn = __shfl_down_sync(0xffffffffu, ql, 1);
     const int qr = (i == o_nb - 1) ? kOne : qn;
     const int w = qr - ql;
-    if (lane < 31 && idx < total && w > 0 && j >= 0 && j < C.nbins)
+    if (lane < 31 && idx < total && w > 0 && j >= 0 && j < C.nbins &&
+        PV_CHECK(j < C.ntiles * 32, 2))
       atomicAdd(hist + j, static_cast<uint32_t>(w));
   }
 }
@@ -476,6 +492,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
   int n_starts = 0, n_ends = 0, n_done = 0;
 
   auto put = [&](int pos, int lo, int hi, int im) {
+    if (!PV_CHECK(pos >= 0 && pos < kMaxSeeds && im >= 0 && im < C.nbins, 4)) return;
     const uint32_t nm = bin_or_zero(N, im - 1, C), ni = N[im], np = bin_or_zero(N, im + 1, C);
     S->lo[pos] = lo;
     S->hi[pos] = hi;
@@ -586,7 +603,8 @@ __device__ int block_associate(const CenterT* center, CidT* cid, int n, SeedOut*
   __syncthreads();
   for (;;) {
     int ka = s_ka;
-    if (tid + 1 < ka) part[tid] = (S->hi[alive[tid]] + S->lo[alive[tid + 1]]) >> 1;
+    if (tid + 1 < ka && PV_CHECK(ka <= kMaxSeeds, 5))
+      part[tid] = (S->hi[alive[tid]] + S->lo[alive[tid + 1]]) >> 1;
     if (tid < ka) cnt[tid] = 0;
     __syncthreads();
     for (int t = tid; t < n; t += nt) {

@@ -16,9 +16,37 @@
 // global memory: the per-step design the fused path is measured against.
 #include "pv_kernels.cuh"
 
+#if PV_CHECKED
+// out-of-bounds indices met by the checked build: their number and the code
+// of the first one
+__device__ unsigned int g_check_count;
+__device__ unsigned int g_check_first;
+namespace pvdev {
+__device__ void check_failed(unsigned code) {
+  if (atomicAdd(&g_check_count, 1u) == 0u) g_check_first = code;
+}
+}  // namespace pvdev
+#endif
+
 namespace pvk {
 
 using namespace pvdev;
+
+bool check_report(unsigned* count, unsigned* first) {
+#if PV_CHECKED
+  unsigned zero = 0;
+  cudaDeviceSynchronize();
+  cudaMemcpyFromSymbol(count, g_check_count, sizeof(unsigned));
+  cudaMemcpyFromSymbol(first, g_check_first, sizeof(unsigned));
+  cudaMemcpyToSymbol(g_check_count, &zero, sizeof(unsigned));
+  cudaMemcpyToSymbol(g_check_first, &zero, sizeof(unsigned));
+  return true;
+#else
+  *count = 0;
+  *first = 0;
+  return false;
+#endif
+}
 
 // ---------------------------------------------------------------------------
 // shared-memory layout of the find kernel
@@ -113,7 +141,7 @@ __device__ __forceinline__ void warp_place(const CidT* cid, int n, int* base, in
     int b = c >= 0 ? base[c] : 0;
     __syncwarp();
     if (c >= 0) {
-      sorted[b0 + b + rank] = static_cast<int32_t>(b0 + t);
+      if (PV_CHECK(b + rank < n, 6)) sorted[b0 + b + rank] = static_cast<int32_t>(b0 + t);
       if (lane == leader) base[c] = b + __popc(peers);
     }
     __syncwarp();
@@ -301,14 +329,16 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
         p.tq = 0;
         if (t < n) {
           p = prepare_track<PROFILE>(c0, c1, c2, c3, c4, c5, c6, c7, C);
-          center[t] = static_cast<int16_t>(p.filled ? p.center : -1);
+          if (PV_CHECK(!small || t < kSmallCap, 7))
+            center[t] = static_cast<int16_t>(p.filled ? p.center : -1);
         }
         if (p.filled) {
           int q0 = (p.j0 < 0 ? 0 : p.j0) >> 5;
           int q1 = (p.j1 >= C.nbins ? C.nbins - 1 : p.j1) >> 5;
           for (int q = q0; q <= q1; ++q) {
             uint32_t bit = 1u << (q & 31);
-            if (!(tmask[q >> 5] & bit)) atomicOr(tmask + (q >> 5), bit);
+            if (PV_CHECK((q >> 5) < kTileWords, 8) && !(tmask[q >> 5] & bit))
+              atomicOr(tmask + (q >> 5), bit);
           }
         }
         warp_fill_profiles<PROFILE>(hist, p.zpoca, p.sigma, p.j0,
@@ -429,7 +459,7 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
                 w.c = __float_as_uint(S->z[k]);
               }
               w.pad = 0;
-              G.work[class_pick(G.cls_base, cl) + idx] = w;
+              if (PV_CHECK(idx >= 0, 9)) G.work[class_pick(G.cls_base, cl) + idx] = w;
             }
           } else {
             write_empty_vertex(C, O, S, e, k);
@@ -502,10 +532,15 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
       W = G.W + w.off + r;
       stride = kGroup;
     }
+    // (a checked build that finds a bad vertex range fits no track for it;
+    // the warp stays converged for the fit's shuffles)
+    const int cnt_g = PV_CHECK(cntk <= 0 || (w.off >= 0 && w.off + cntk <= T.n_tracks), 11)
+                          ? cntk : 0;
     // two tracks per pass: both tracks' loads are in flight together
     int s = r, q = 0;
-    for (; s + kGroup < cntk; s += 2 * kGroup, q += 2 * stride) {
+    for (; s + kGroup < cnt_g; s += 2 * kGroup, q += 2 * stride) {
       const int t0 = G.sorted[w.off + s], t1 = G.sorted[w.off + s + kGroup];
+      if (!PV_CHECK(t0 >= 0 && t0 < T.n_tracks && t1 >= 0 && t1 < T.n_tracks, 12)) break;
       const float a0 = T.x[t0], a1 = T.y[t0], a2 = T.z[t0], a3 = T.tx[t0], a4 = T.ty[t0];
       const float a5 = T.cxx[t0], a6 = T.cxtx[t0], a7 = T.ctxtx[t0], a8 = T.cyy[t0];
       const float a9 = T.cyty[t0], a10 = T.ctyty[t0];
@@ -516,13 +551,14 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
       make_fit_track(b0, b1, b2, b3, b4, b5, b6, b7, b8, b9, b10, xs, ys, zs, A + q + stride,
                      W + q + stride);
     }
-    if (s < cntk) {
+    if (s < cnt_g) {
       const int t = G.sorted[w.off + s];
-      make_fit_track(T.x[t], T.y[t], T.z[t], T.tx[t], T.ty[t], T.cxx[t], T.cxtx[t], T.ctxtx[t],
-                     T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, A + q, W + q);
+      if (PV_CHECK(t >= 0 && t < T.n_tracks, 12))
+        make_fit_track(T.x[t], T.y[t], T.z[t], T.tx[t], T.ty[t], T.cxx[t], T.cxtx[t],
+                       T.ctxtx[t], T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, A + q, W + q);
     }
     VertexOut out;
-    group_fit<kAccum>(A, W, stride, cntk, C, &out);
+    group_fit<kAccum>(A, W, stride, cnt_g, C, &out);
     if (has && r == 0) write_vertex(C, O, w.e, k, xs, ys, zs, out);
   }
 }
@@ -767,7 +803,8 @@ mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
     wb = K > 0 ? atomicAdd(M.counters, K) : 0;
   }
   wb = __shfl_sync(0xffffffffu, wb, 0);
-  for (int k = lane; k < K; k += 32) M.work[wb + k] = make_int2(e, k);
+  for (int k = lane; k < K; k += 32)
+    if (PV_CHECK(K <= kMaxSeeds, 13)) M.work[wb + k] = make_int2(e, k);
 }
 
 // Multi-vertex fits from the work list: every 8-lane group fits one vertex,

@@ -142,6 +142,10 @@ cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, c
                          const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
                          cudaStream_t st, int* n_launches);
 
+// The checked build's record of out-of-bounds indices (count, first code),
+// reset by the call; false in the default build, which has no checks.
+bool check_report(unsigned* count, unsigned* first);
+
 bool find_block_ok(int nt);
 bool fit_block_ok(int ft);
 int fused_blocks_per_sm(int nbins, int mode, int nt, int flav);

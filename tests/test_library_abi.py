@@ -156,3 +156,22 @@ def test_product_path_does_not_import_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "oracle/" not in src, f
                 assert "pv_oracle" not in src, f
+
+
+def test_default_build_has_no_bounds_checks(lib):
+    """pv_check_report answers PV_ERR_ARG with zeros in the default build (no
+    device call is made)."""
+    import paper_2412_14966_gb300 as pv
+    assert pv.check_report() == (False, 0, 0)
+
+
+def test_checked_build_compiles_with_the_same_exports():
+    """The checked test build (PV_CHECKED=1) compiles for sm_103a and exports
+    every function the header declares."""
+    from paper_2412_14966_gb300 import build
+    path = build.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    names = set(re.findall(r"\bpv_\w+", out))
+    declared = set(re.findall(r"\b(pv_\w+)\s*\(", open(HEADER).read()))
+    assert declared <= names, declared - names
