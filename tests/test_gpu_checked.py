@@ -67,9 +67,12 @@ def _close_multi(a, b, E):
     if not np.array_equal(a["n_per_event"][:E], b["n_per_event"][:E]):
         return False
     live = np.arange(a["x"].shape[1])[None, :] < a["n_per_event"][:E, None]
-    d = np.maximum(np.abs(a["x"][:E] - b["x"][:E]), np.abs(a["y"][:E] - b["y"][:E]))[live]
-    dz = np.abs(a["z"][:E] - b["z"][:E])[live]
-    bad = (d >= 1e-4) | (dz >= 5e-4)
+    bad = np.zeros(int(live.sum()), bool)
+    for k, tol in (("x", 1e-4), ("y", 1e-4), ("z", 5e-4)):
+        u, v = a[k][:E][live].astype(np.float64), b[k][:E][live].astype(np.float64)
+        both_nan = np.isnan(u) & np.isnan(v)     # singular vertices carry no position
+        with np.errstate(invalid="ignore"):
+            bad |= ~both_nan & ~(np.abs(u - v) < tol)
     return bad.sum() <= max(2, 0.002 * live.sum())
 
 
