@@ -522,10 +522,15 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     const uint64_t t_min = C.t_pp < C.t_gas ? C.t_pp : C.t_gas;
     const bool walk = lane < count && total >= t_min;
     int kept = 0, lo1 = 0, hi1 = 0, im1 = 0;
+    int lo2 = 0, hi2 = 0, im2 = 0;   // the recursive split also keeps the second piece
     if (walk) {
       split_pieces<kSplit>(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
         if (keep_piece(integral, im, C)) {
-          if (kept == 0) { lo1 = lo; hi1 = hi; im1 = im; }
+          if (kept == 0) {
+            lo1 = lo; hi1 = hi; im1 = im;
+          } else if constexpr (kSplit == PV_SPLIT_RECURSIVE) {
+            if (kept == 1) { lo2 = lo; hi2 = hi; im2 = im; }
+          }
           ++kept;
         }
       });
@@ -537,9 +542,18 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     }
     int n_kept = __shfl_sync(0xffffffffu, incl, 31);
     int pos = n_seeds + incl - kept;
+    bool rewalk = kept > 1 && pos < cap;
     if (kept == 1 && pos < cap) {
       put(pos, lo1, hi1, im1);
-    } else if (kept > 1 && pos < cap) {
+    } else if constexpr (kSplit == PV_SPLIT_RECURSIVE) {
+      // the recursive split is the costlier walk: two pieces need none again
+      if (kept == 2 && pos < cap) {
+        put(pos, lo1, hi1, im1);
+        if (pos + 1 < cap) put(pos + 1, lo2, hi2, im2);
+        rewalk = false;
+      }
+    }
+    if (rewalk) {
       split_pieces<kSplit>(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
         if (keep_piece(integral, im, C)) {
           if (pos < cap) put(pos, lo, hi, im);
