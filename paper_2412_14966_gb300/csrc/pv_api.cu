@@ -148,6 +148,8 @@ struct PlainLayout {
 // ---- serving --------------------------------------------------------------
 
 constexpr int kServeStreams = 4;
+constexpr int kRunHostChunks = 4;           // pv_run_host: event chunks in flight
+constexpr int64_t kRunHostChunkEvents = 2048;  // fewest events per chunk
 constexpr size_t kMaxQueued = 4096;
 
 struct Request {
@@ -224,6 +226,12 @@ struct pv_ctx {
   // host-buffer entry point staging
   DevBuf host_in, host_out;
   cudaStream_t own_stream = nullptr;
+  // pv_run_host's pipeline: copy-in and copy-out streams, per-chunk events and
+  // the chunks' event offsets (pinned host memory)
+  cudaStream_t rh_in = nullptr, rh_out = nullptr;
+  cudaEvent_t rh_ev[2 * kRunHostChunks + 1] = {};
+  int64_t* rh_off = nullptr;
+  size_t rh_off_cap = 0;
   std::atomic<uint64_t> launches{0};
   std::string last_error;
   // serving
@@ -678,6 +686,11 @@ int pv_destroy(pv_ctx* ctx) {
   ctx->tpl.release();
   ctx->host_in.release();
   ctx->host_out.release();
+  if (ctx->rh_in) cudaStreamDestroy(ctx->rh_in);
+  if (ctx->rh_out) cudaStreamDestroy(ctx->rh_out);
+  for (auto& ev : ctx->rh_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->rh_off) cudaFreeHost(ctx->rh_off);
   ctx->pool.release();
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete ctx;
@@ -820,68 +833,146 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
   const int64_t n = h->n_tracks;
   const int64_t E = h->n_events;
   const size_t cap = static_cast<size_t>(ho->capacity);
-  // device inputs: 11 float arrays + offsets
-  size_t in_bytes = 11 * round16(4 * n) + round16(8 * (E + 1));
+  const int64_t* hoff = h->event_offsets;
+  // events in K chunks, pipelined: chunk k's inputs copy in while chunk k-1
+  // runs and chunk k-2's results copy out.  Chunks need offsets that rise
+  // within [0, n]; other batches run as one chunk (their kernels flag the
+  // events with bad offsets).
+  int K = 1;
+  if (E >= 2 * kRunHostChunkEvents && hoff[0] == 0 && hoff[E] <= n) {
+    bool rising = true;
+    for (int64_t e = 0; e < E && rising; ++e) rising = hoff[e + 1] >= hoff[e];
+    if (rising) {
+      const int64_t k = E / kRunHostChunkEvents;
+      K = static_cast<int>(k < kRunHostChunks ? k : kRunHostChunks);
+    }
+  }
+  // device inputs: 11 float arrays + the chunks' offsets (E + K entries)
+  size_t in_bytes = 11 * round16(4 * n) + round16(8 * (E + K));
   PV_CUDA(ctx, ctx->host_in.ensure(in_bytes));
   char* din = static_cast<char*>(ctx->host_in.p);
   const float* src[11] = {h->x, h->y, h->z, h->tx, h->ty, h->cxx, h->cxtx, h->ctxtx,
                           h->cyy, h->cyty, h->ctyty};
   float* dcol[11];
-  for (int k = 0; k < 11; ++k) {
-    dcol[k] = reinterpret_cast<float*>(din + k * round16(4 * n));
-    if (n) PV_CUDA(ctx, cudaMemcpyAsync(dcol[k], src[k], 4 * n, cudaMemcpyHostToDevice, st));
-  }
+  for (int k = 0; k < 11; ++k) dcol[k] = reinterpret_cast<float*>(din + k * round16(4 * n));
   int64_t* doff = reinterpret_cast<int64_t*>(din + 11 * round16(4 * n));
-  if (E) PV_CUDA(ctx, cudaMemcpyAsync(doff, h->event_offsets, 8 * (E + 1), cudaMemcpyHostToDevice, st));
-  pv_tracks dt = *h;
-  dt.x = dcol[0]; dt.y = dcol[1]; dt.z = dcol[2]; dt.tx = dcol[3]; dt.ty = dcol[4];
-  dt.cxx = dcol[5]; dt.cxtx = dcol[6]; dt.ctxtx = dcol[7];
-  dt.cyy = dcol[8]; dt.cyty = dcol[9]; dt.ctyty = dcol[10];
-  dt.event_offsets = doff;
-  // device outputs mirror the non-NULL host outputs
-  const size_t nv = static_cast<size_t>(E) * cap;
-  struct Col { void* host; size_t bytes; } cols[16];
+  // device outputs mirror the non-NULL host outputs; per slot [event][cap],
+  // per event, or per track
+  enum Unit { kSlot, kEvent, kTrack };
+  struct Col { void* host; size_t elem; Unit unit; size_t off; } cols[16];
   int nc = 0;
   size_t o = 0;
-  auto plan = [&](void* hp, size_t bytes) -> size_t {
+  auto plan = [&](void* hp, size_t elem, Unit u) -> size_t {
     size_t off = o;
-    if (hp) { cols[nc++] = {hp, bytes}; o += round16(bytes); }
+    if (hp) {
+      const size_t count = u == kSlot ? static_cast<size_t>(E) * cap
+                                      : (u == kEvent ? static_cast<size_t>(E)
+                                                     : static_cast<size_t>(n));
+      cols[nc++] = {hp, elem, u, off};
+      o += round16(elem * count);
+    }
     return off;
   };
-  size_t ox = plan(ho->x, 4 * nv), oy = plan(ho->y, 4 * nv), oz = plan(ho->z, 4 * nv);
-  size_t ocov = plan(ho->cov, 24 * nv), ochi = plan(ho->chi2, 4 * nv), ondf = plan(ho->ndof, 4 * nv);
-  size_t ontr = plan(ho->n_tracks, 4 * nv), onit = plan(ho->n_iter, 4 * nv);
-  size_t ost = plan(ho->status, 4 * nv), olo = plan(ho->bin_lo, 4 * nv);
-  size_t ohi = plan(ho->bin_hi, 4 * nv), obm = plan(ho->bin_max, 4 * nv);
-  size_t onpe = plan(ho->n_per_event, 4 * E), oevs = plan(ho->event_status, 4 * E);
-  size_t otv = plan(ho->track_vertex, 4 * n);
+  size_t ox = plan(ho->x, 4, kSlot), oy = plan(ho->y, 4, kSlot), oz = plan(ho->z, 4, kSlot);
+  size_t ocov = plan(ho->cov, 24, kSlot), ochi = plan(ho->chi2, 4, kSlot);
+  size_t ondf = plan(ho->ndof, 4, kSlot), ontr = plan(ho->n_tracks, 4, kSlot);
+  size_t onit = plan(ho->n_iter, 4, kSlot), ost = plan(ho->status, 4, kSlot);
+  size_t olo = plan(ho->bin_lo, 4, kSlot), ohi = plan(ho->bin_hi, 4, kSlot);
+  size_t obm = plan(ho->bin_max, 4, kSlot);
+  size_t onpe = plan(ho->n_per_event, 4, kEvent), oevs = plan(ho->event_status, 4, kEvent);
+  size_t otv = plan(ho->track_vertex, 4, kTrack);
   PV_CUDA(ctx, ctx->host_out.ensure(o + 16));
   char* dout = static_cast<char*>(ctx->host_out.p);
-  pv_vertices dv = *ho;
-  auto dp = [&](void* hp, size_t off) -> void* { return hp ? dout + off : nullptr; };
-  dv.x = static_cast<float*>(dp(ho->x, ox));
-  dv.y = static_cast<float*>(dp(ho->y, oy));
-  dv.z = static_cast<float*>(dp(ho->z, oz));
-  dv.cov = static_cast<float*>(dp(ho->cov, ocov));
-  dv.chi2 = static_cast<float*>(dp(ho->chi2, ochi));
-  dv.ndof = static_cast<float*>(dp(ho->ndof, ondf));
-  dv.n_tracks = static_cast<int32_t*>(dp(ho->n_tracks, ontr));
-  dv.n_iter = static_cast<int32_t*>(dp(ho->n_iter, onit));
-  dv.status = static_cast<int32_t*>(dp(ho->status, ost));
-  dv.bin_lo = static_cast<int32_t*>(dp(ho->bin_lo, olo));
-  dv.bin_hi = static_cast<int32_t*>(dp(ho->bin_hi, ohi));
-  dv.bin_max = static_cast<int32_t*>(dp(ho->bin_max, obm));
-  dv.n_per_event = static_cast<int32_t*>(dp(ho->n_per_event, onpe));
-  dv.event_status = static_cast<int32_t*>(dp(ho->event_status, oevs));
-  dv.track_vertex = static_cast<int32_t*>(dp(ho->track_vertex, otv));
-  rc = run_find_or_fit(ctx, &dt, nullptr, &dv, st, pvk::kFindFit);
-  if (rc != PV_OK) return rc;
-  size_t off = 0;
-  for (int k = 0; k < nc; ++k) {
-    if (cols[k].bytes)
-      PV_CUDA(ctx, cudaMemcpyAsync(cols[k].host, dout + off, cols[k].bytes, cudaMemcpyDeviceToHost, st));
-    off += round16(cols[k].bytes);
+  auto dp = [&](void* hp, size_t off) -> char* { return hp ? dout + off : nullptr; };
+
+  if (K > 1) {
+    if (!ctx->rh_in)
+      PV_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->rh_in, cudaStreamNonBlocking));
+    if (!ctx->rh_out)
+      PV_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->rh_out, cudaStreamNonBlocking));
+    for (auto& ev : ctx->rh_ev)
+      if (!ev) PV_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    const size_t need = static_cast<size_t>(E + K);
+    if (ctx->rh_off_cap < need) {
+      if (ctx->rh_off) cudaFreeHost(ctx->rh_off);
+      ctx->rh_off = nullptr;
+      ctx->rh_off_cap = 0;
+      PV_CUDA(ctx, cudaMallocHost(&ctx->rh_off, sizeof(int64_t) * need));
+      ctx->rh_off_cap = need;
+    }
+    // the copies start after the caller's earlier work on its stream
+    PV_CUDA(ctx, cudaEventRecord(ctx->rh_ev[2 * kRunHostChunks], st));
+    PV_CUDA(ctx, cudaStreamWaitEvent(ctx->rh_in, ctx->rh_ev[2 * kRunHostChunks], 0));
   }
+  for (int k = 0; k < K; ++k) {
+    const int64_t e0 = E * k / K, e1 = E * (k + 1) / K;
+    const int64_t b0 = K > 1 ? hoff[e0] : 0, b1 = K > 1 ? hoff[e1] : n;
+    cudaStream_t s_in = K > 1 ? ctx->rh_in : st;
+    cudaStream_t s_out = K > 1 ? ctx->rh_out : st;
+    const int64_t nt = b1 - b0;
+    for (int c = 0; c < 11; ++c)
+      if (nt) PV_CUDA(ctx, cudaMemcpyAsync(dcol[c] + b0, src[c] + b0, 4 * nt,
+                                           cudaMemcpyHostToDevice, s_in));
+    // chunk k's offsets, relative to its first track, at entries e0 + k ..
+    int64_t* doff_k = doff + e0 + k;
+    if (K > 1) {
+      int64_t* ho_k = ctx->rh_off + e0 + k;
+      for (int64_t e = e0; e <= e1; ++e) ho_k[e - e0] = hoff[e] - b0;
+      PV_CUDA(ctx, cudaMemcpyAsync(doff_k, ho_k, 8 * (e1 - e0 + 1), cudaMemcpyHostToDevice,
+                                   s_in));
+      PV_CUDA(ctx, cudaEventRecord(ctx->rh_ev[k], s_in));
+      PV_CUDA(ctx, cudaStreamWaitEvent(st, ctx->rh_ev[k], 0));
+    } else if (E) {
+      PV_CUDA(ctx, cudaMemcpyAsync(doff_k, hoff, 8 * (E + 1), cudaMemcpyHostToDevice, st));
+    }
+    pv_tracks dt = *h;
+    dt.x = dcol[0] + b0; dt.y = dcol[1] + b0; dt.z = dcol[2] + b0;
+    dt.tx = dcol[3] + b0; dt.ty = dcol[4] + b0;
+    dt.cxx = dcol[5] + b0; dt.cxtx = dcol[6] + b0; dt.ctxtx = dcol[7] + b0;
+    dt.cyy = dcol[8] + b0; dt.cyty = dcol[9] + b0; dt.ctyty = dcol[10] + b0;
+    dt.event_offsets = doff_k;
+    dt.n_tracks = nt;
+    dt.n_events = static_cast<int32_t>(e1 - e0);
+    const size_t slot0 = static_cast<size_t>(e0) * cap;
+    auto sp = [&](void* hp, size_t off, size_t elem, size_t first) -> void* {
+      char* d = dp(hp, off);
+      return d ? d + elem * first : nullptr;
+    };
+    pv_vertices dv = *ho;
+    dv.x = static_cast<float*>(sp(ho->x, ox, 4, slot0));
+    dv.y = static_cast<float*>(sp(ho->y, oy, 4, slot0));
+    dv.z = static_cast<float*>(sp(ho->z, oz, 4, slot0));
+    dv.cov = static_cast<float*>(sp(ho->cov, ocov, 24, slot0));
+    dv.chi2 = static_cast<float*>(sp(ho->chi2, ochi, 4, slot0));
+    dv.ndof = static_cast<float*>(sp(ho->ndof, ondf, 4, slot0));
+    dv.n_tracks = static_cast<int32_t*>(sp(ho->n_tracks, ontr, 4, slot0));
+    dv.n_iter = static_cast<int32_t*>(sp(ho->n_iter, onit, 4, slot0));
+    dv.status = static_cast<int32_t*>(sp(ho->status, ost, 4, slot0));
+    dv.bin_lo = static_cast<int32_t*>(sp(ho->bin_lo, olo, 4, slot0));
+    dv.bin_hi = static_cast<int32_t*>(sp(ho->bin_hi, ohi, 4, slot0));
+    dv.bin_max = static_cast<int32_t*>(sp(ho->bin_max, obm, 4, slot0));
+    dv.n_per_event = static_cast<int32_t*>(sp(ho->n_per_event, onpe, 4, e0));
+    dv.event_status = static_cast<int32_t*>(sp(ho->event_status, oevs, 4, e0));
+    dv.track_vertex = static_cast<int32_t*>(sp(ho->track_vertex, otv, 4, b0));
+    rc = run_find_or_fit(ctx, &dt, nullptr, &dv, st, pvk::kFindFit);
+    if (rc != PV_OK) return rc;
+    if (K > 1) {
+      PV_CUDA(ctx, cudaEventRecord(ctx->rh_ev[kRunHostChunks + k], st));
+      PV_CUDA(ctx, cudaStreamWaitEvent(s_out, ctx->rh_ev[kRunHostChunks + k], 0));
+    }
+    for (int c = 0; c < nc; ++c) {
+      const Col& col = cols[c];
+      size_t first, count;
+      if (col.unit == kSlot) { first = slot0; count = static_cast<size_t>(e1 - e0) * cap; }
+      else if (col.unit == kEvent) { first = e0; count = static_cast<size_t>(e1 - e0); }
+      else { first = b0; count = static_cast<size_t>(nt); }
+      if (count)
+        PV_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(col.host) + col.elem * first,
+                                     dout + col.off + col.elem * first, col.elem * count,
+                                     cudaMemcpyDeviceToHost, s_out));
+    }
+  }
+  if (K > 1) PV_CUDA(ctx, cudaStreamSynchronize(ctx->rh_out));
   PV_CUDA(ctx, cudaStreamSynchronize(st));
   return PV_OK;
 }

@@ -369,3 +369,46 @@ def test_template_profile_flavour(pv, path, split):
         fit = oracle.fit_batch(batch, ref, p)
         G.assert_fit_close(v, fit, ref["n"], lambda: _tight(pv, batch, s, ref, **cfg),
                            cond=(batch, ref, p))
+
+
+@pytest.mark.parametrize("case", ["nominal", "mixture", "unsplittable"])
+def test_run_host_pipeline_equals_device_path(pv, case):
+    """pv_run_host splits batches of 4,096 events or more into event chunks
+    whose copies overlap the kernels; the results equal the device path's bit
+    for bit (events are independent).  A batch whose offsets do not rise runs
+    as one chunk and still matches (its bad event flagged the same way)."""
+    import torch
+    if case == "nominal":
+        batch = synthetic.workload_nominal(n_events=9000, seed=12)
+    elif case == "mixture":
+        batch = synthetic.workload_mixture(n_events=5000, seed=13)
+    else:
+        batch = synthetic.workload_nominal(n_events=4500, seed=14)
+        off = batch.offsets.copy()
+        off[-1] = off[-1] + 5            # the last event ends past the last track
+        batch.offsets = off
+    ctx = pv.Context(device=0, use_graph=1)
+    s, v = G.gpu_find_fit(ctx, batch)
+    host = pv.Tracks.from_host(batch)
+    out = pv.Vertices.empty(batch.n_events, batch.n_tracks, host=True, pinned=True)
+    for a in out.a.values():
+        a.fill_(-7)
+    ctx.run_host(host, out)
+    ctx.close()
+    o = out.numpy()
+    E = batch.n_events
+    assert np.array_equal(o["n_per_event"][:E], v["n_per_event"][:E])
+    assert np.array_equal(o["event_status"][:E], v["event_status"][:E])
+    for e in range(E):
+        n = v["n_per_event"][e]
+        for k in ("x", "y", "z", "cov", "chi2", "status", "n_iter", "n_tracks"):
+            assert np.array_equal(o[k][e, :n], v[k][e, :n]), (k, e)
+    nt = len(batch.tracks["x"])
+    owned = np.zeros(nt, bool)
+    for e in range(E):
+        b0, b1 = batch.offsets[e], batch.offsets[e + 1]
+        if 0 <= b0 <= b1 <= nt:
+            owned[b0:b1] = True
+    assert np.array_equal(o["track_vertex"][:nt][owned], v["track_vertex"][:nt][owned])
+    if case == "unsplittable":
+        assert o["event_status"][E - 1] == pv.EV_BAD_OFFSETS
