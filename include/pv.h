@@ -217,10 +217,16 @@ int pv_num_bins(const pv_ctx* ctx);
 int pv_check_report(uint32_t* count, uint32_t* first_code);
 
 /* The whole method through host memory: copies the host SoA tracks to
- * context-owned device buffers, runs the fused find+fit, copies the vertex
- * outputs back into the host pv_vertices and synchronises cuda_stream.  All
+ * context-owned device buffers, runs the fused find+fit, delivers the vertex
+ * outputs into the host pv_vertices and synchronises cuda_stream.  All
  * pointers in tracks and out are host pointers (pinned memory gives
- * asynchronous copies).  Blocking. */
+ * asynchronous copies).  Batches of 4,096 events or more with rising offsets
+ * run as two event chunks whose copies overlap the other chunk's kernels.  On
+ * the fused path, outputs in pinned (CUDA-registered) memory are written by
+ * the kernels in place: only the slots of found vertices (and every event and
+ * track entry) are written, the other slots keep their contents.  Other
+ * outputs, and all outputs of the plain path, are staged on the device and
+ * copied back whole.  Blocking. */
 int pv_run_host(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, void* cuda_stream);
 
 /* Serving.  pv_submit admits a request (device tracks and outputs, borrowed

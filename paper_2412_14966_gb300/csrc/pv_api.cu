@@ -148,7 +148,10 @@ struct PlainLayout {
 // ---- serving --------------------------------------------------------------
 
 constexpr int kServeStreams = 4;
-constexpr int kRunHostChunks = 4;           // pv_run_host: event chunks in flight
+// pv_run_host: event chunks in flight (measured on the nominal batch: 2
+// chunks 0.64 ms per step, 3 0.65, 4 0.69, 8 0.81 — every chunk pays its
+// copies' set-up and the kernels' tail, and the host link is the bound)
+constexpr int kRunHostChunks = 2;
 constexpr int64_t kRunHostChunkEvents = 2048;  // fewest events per chunk
 constexpr size_t kMaxQueued = 4096;
 
@@ -857,33 +860,47 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
   for (int k = 0; k < 11; ++k) dcol[k] = reinterpret_cast<float*>(din + k * round16(4 * n));
   int64_t* doff = reinterpret_cast<int64_t*>(din + 11 * round16(4 * n));
   // device outputs mirror the non-NULL host outputs; per slot [event][cap],
-  // per event, or per track
+  // per event, or per track.  On the fused path, pinned host memory that the
+  // device can address is written by the kernels in place (they write only
+  // the slots of found vertices and read no output back, so nothing is
+  // copied back for it); other host memory, and every output of the plain
+  // path (whose fit reads the find's outputs), gets a device staging buffer
+  // and a copy back.
+  const bool in_place = ctx->cfg.path != PV_PATH_PLAIN;
   enum Unit { kSlot, kEvent, kTrack };
-  struct Col { void* host; size_t elem; Unit unit; size_t off; } cols[16];
+  struct Col { void* host; size_t elem; Unit unit; char* dev; bool direct; } cols[16];
   int nc = 0;
   size_t o = 0;
-  auto plan = [&](void* hp, size_t elem, Unit u) -> size_t {
-    size_t off = o;
-    if (hp) {
-      const size_t count = u == kSlot ? static_cast<size_t>(E) * cap
-                                      : (u == kEvent ? static_cast<size_t>(E)
-                                                     : static_cast<size_t>(n));
-      cols[nc++] = {hp, elem, u, off};
-      o += round16(elem * count);
+  auto plan = [&](void* hp, size_t elem, Unit u) -> int {
+    if (!hp) return -1;
+    cudaPointerAttributes a{};
+    char* alias = nullptr;
+    if (!in_place) {
+      // staged
+    } else if (cudaPointerGetAttributes(&a, hp) == cudaSuccess) {
+      if (a.type == cudaMemoryTypeHost && a.devicePointer) alias = static_cast<char*>(a.devicePointer);
+    } else {
+      cudaGetLastError();   // not a pointer CUDA knows: stage it
     }
-    return off;
+    const size_t count = u == kSlot ? static_cast<size_t>(E) * cap
+                                    : (u == kEvent ? static_cast<size_t>(E)
+                                                   : static_cast<size_t>(n));
+    cols[nc] = {hp, elem, u, alias ? alias : reinterpret_cast<char*>(o), alias != nullptr};
+    if (!alias) o += round16(elem * count);
+    return nc++;
   };
-  size_t ox = plan(ho->x, 4, kSlot), oy = plan(ho->y, 4, kSlot), oz = plan(ho->z, 4, kSlot);
-  size_t ocov = plan(ho->cov, 24, kSlot), ochi = plan(ho->chi2, 4, kSlot);
-  size_t ondf = plan(ho->ndof, 4, kSlot), ontr = plan(ho->n_tracks, 4, kSlot);
-  size_t onit = plan(ho->n_iter, 4, kSlot), ost = plan(ho->status, 4, kSlot);
-  size_t olo = plan(ho->bin_lo, 4, kSlot), ohi = plan(ho->bin_hi, 4, kSlot);
-  size_t obm = plan(ho->bin_max, 4, kSlot);
-  size_t onpe = plan(ho->n_per_event, 4, kEvent), oevs = plan(ho->event_status, 4, kEvent);
-  size_t otv = plan(ho->track_vertex, 4, kTrack);
+  const int ix = plan(ho->x, 4, kSlot), iy = plan(ho->y, 4, kSlot), iz = plan(ho->z, 4, kSlot);
+  const int icov = plan(ho->cov, 24, kSlot), ichi = plan(ho->chi2, 4, kSlot);
+  const int indf = plan(ho->ndof, 4, kSlot), intr = plan(ho->n_tracks, 4, kSlot);
+  const int init = plan(ho->n_iter, 4, kSlot), ist = plan(ho->status, 4, kSlot);
+  const int ilo = plan(ho->bin_lo, 4, kSlot), ihi = plan(ho->bin_hi, 4, kSlot);
+  const int ibm = plan(ho->bin_max, 4, kSlot);
+  const int inpe = plan(ho->n_per_event, 4, kEvent), ievs = plan(ho->event_status, 4, kEvent);
+  const int itv = plan(ho->track_vertex, 4, kTrack);
   PV_CUDA(ctx, ctx->host_out.ensure(o + 16));
   char* dout = static_cast<char*>(ctx->host_out.p);
-  auto dp = [&](void* hp, size_t off) -> char* { return hp ? dout + off : nullptr; };
+  for (int c = 0; c < nc; ++c)
+    if (!cols[c].direct) cols[c].dev = dout + reinterpret_cast<size_t>(cols[c].dev);
 
   if (K > 1) {
     if (!ctx->rh_in)
@@ -934,26 +951,25 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
     dt.n_tracks = nt;
     dt.n_events = static_cast<int32_t>(e1 - e0);
     const size_t slot0 = static_cast<size_t>(e0) * cap;
-    auto sp = [&](void* hp, size_t off, size_t elem, size_t first) -> void* {
-      char* d = dp(hp, off);
-      return d ? d + elem * first : nullptr;
+    auto sp = [&](int c, size_t first) -> void* {
+      return c < 0 ? nullptr : cols[c].dev + cols[c].elem * first;
     };
     pv_vertices dv = *ho;
-    dv.x = static_cast<float*>(sp(ho->x, ox, 4, slot0));
-    dv.y = static_cast<float*>(sp(ho->y, oy, 4, slot0));
-    dv.z = static_cast<float*>(sp(ho->z, oz, 4, slot0));
-    dv.cov = static_cast<float*>(sp(ho->cov, ocov, 24, slot0));
-    dv.chi2 = static_cast<float*>(sp(ho->chi2, ochi, 4, slot0));
-    dv.ndof = static_cast<float*>(sp(ho->ndof, ondf, 4, slot0));
-    dv.n_tracks = static_cast<int32_t*>(sp(ho->n_tracks, ontr, 4, slot0));
-    dv.n_iter = static_cast<int32_t*>(sp(ho->n_iter, onit, 4, slot0));
-    dv.status = static_cast<int32_t*>(sp(ho->status, ost, 4, slot0));
-    dv.bin_lo = static_cast<int32_t*>(sp(ho->bin_lo, olo, 4, slot0));
-    dv.bin_hi = static_cast<int32_t*>(sp(ho->bin_hi, ohi, 4, slot0));
-    dv.bin_max = static_cast<int32_t*>(sp(ho->bin_max, obm, 4, slot0));
-    dv.n_per_event = static_cast<int32_t*>(sp(ho->n_per_event, onpe, 4, e0));
-    dv.event_status = static_cast<int32_t*>(sp(ho->event_status, oevs, 4, e0));
-    dv.track_vertex = static_cast<int32_t*>(sp(ho->track_vertex, otv, 4, b0));
+    dv.x = static_cast<float*>(sp(ix, slot0));
+    dv.y = static_cast<float*>(sp(iy, slot0));
+    dv.z = static_cast<float*>(sp(iz, slot0));
+    dv.cov = static_cast<float*>(sp(icov, slot0));
+    dv.chi2 = static_cast<float*>(sp(ichi, slot0));
+    dv.ndof = static_cast<float*>(sp(indf, slot0));
+    dv.n_tracks = static_cast<int32_t*>(sp(intr, slot0));
+    dv.n_iter = static_cast<int32_t*>(sp(init, slot0));
+    dv.status = static_cast<int32_t*>(sp(ist, slot0));
+    dv.bin_lo = static_cast<int32_t*>(sp(ilo, slot0));
+    dv.bin_hi = static_cast<int32_t*>(sp(ihi, slot0));
+    dv.bin_max = static_cast<int32_t*>(sp(ibm, slot0));
+    dv.n_per_event = static_cast<int32_t*>(sp(inpe, e0));
+    dv.event_status = static_cast<int32_t*>(sp(ievs, e0));
+    dv.track_vertex = static_cast<int32_t*>(sp(itv, b0));
     rc = run_find_or_fit(ctx, &dt, nullptr, &dv, st, pvk::kFindFit);
     if (rc != PV_OK) return rc;
     if (K > 1) {
@@ -962,13 +978,14 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
     }
     for (int c = 0; c < nc; ++c) {
       const Col& col = cols[c];
+      if (col.direct) continue;
       size_t first, count;
       if (col.unit == kSlot) { first = slot0; count = static_cast<size_t>(e1 - e0) * cap; }
       else if (col.unit == kEvent) { first = e0; count = static_cast<size_t>(e1 - e0); }
       else { first = b0; count = static_cast<size_t>(nt); }
       if (count)
         PV_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(col.host) + col.elem * first,
-                                     dout + col.off + col.elem * first, col.elem * count,
+                                     col.dev + col.elem * first, col.elem * count,
                                      cudaMemcpyDeviceToHost, s_out));
     }
   }

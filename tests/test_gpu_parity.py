@@ -246,11 +246,14 @@ def test_bad_offsets_flagged(ctx, pv):
     assert o["event_status"][0] != pv.EV_BAD_OFFSETS
 
 
-def test_run_host_equals_device_path(ctx, pv, small):
+@pytest.mark.parametrize("pinned", [True, False])
+def test_run_host_equals_device_path(ctx, pv, small, pinned):
+    """Pinned host outputs are written by the kernels in place, pageable ones
+    through a device staging buffer; both equal the device path."""
     import torch
     s, v = G.gpu_find_fit(ctx, small)
-    host = pv.Tracks.from_host(small)
-    out = pv.Vertices.empty(small.n_events, small.n_tracks, host=True, pinned=True)
+    host = pv.Tracks.from_host(small, pinned=pinned)
+    out = pv.Vertices.empty(small.n_events, small.n_tracks, host=True, pinned=pinned)
     ctx.run_host(host, out)
     o = out.numpy()
     for e in range(small.n_events):
@@ -371,14 +374,18 @@ def test_template_profile_flavour(pv, path, split):
                            cond=(batch, ref, p))
 
 
-@pytest.mark.parametrize("case", ["nominal", "mixture", "unsplittable"])
+@pytest.mark.parametrize("case", ["nominal", "mixture", "unsplittable", "pageable", "plain",
+                                  "mixed"])
 def test_run_host_pipeline_equals_device_path(pv, case):
     """pv_run_host splits batches of 4,096 events or more into event chunks
     whose copies overlap the kernels; the results equal the device path's bit
     for bit (events are independent).  A batch whose offsets do not rise runs
-    as one chunk and still matches (its bad event flagged the same way)."""
+    as one chunk and still matches (its bad event flagged the same way).
+    Outputs in pinned memory are written in place, pageable ones (and all of
+    the plain path's) are staged and copied back; "mixed" has both kinds in one
+    call."""
     import torch
-    if case == "nominal":
+    if case in ("nominal", "pageable", "plain", "mixed"):
         batch = synthetic.workload_nominal(n_events=9000, seed=12)
     elif case == "mixture":
         batch = synthetic.workload_mixture(n_events=5000, seed=13)
@@ -387,10 +394,14 @@ def test_run_host_pipeline_equals_device_path(pv, case):
         off = batch.offsets.copy()
         off[-1] = off[-1] + 5            # the last event ends past the last track
         batch.offsets = off
-    ctx = pv.Context(device=0, use_graph=1)
+    cfg = dict(path=pv.PATH_PLAIN) if case == "plain" else dict(use_graph=1)
+    ctx = pv.Context(device=0, **cfg)
     s, v = G.gpu_find_fit(ctx, batch)
-    host = pv.Tracks.from_host(batch)
-    out = pv.Vertices.empty(batch.n_events, batch.n_tracks, host=True, pinned=True)
+    host = pv.Tracks.from_host(batch, pinned=case != "pageable")
+    out = pv.Vertices.empty(batch.n_events, batch.n_tracks, host=True, pinned=case != "pageable")
+    if case == "mixed":
+        for k in ("cov", "status", "track_vertex"):
+            out.a[k] = torch.empty_like(out.a[k], pin_memory=False)
     for a in out.a.values():
         a.fill_(-7)
     ctx.run_host(host, out)
