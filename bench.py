@@ -51,13 +51,16 @@ def _peaks():
 
 
 def _sources_hash() -> str:
+    """Hash of the device code the fused kernels are built from (the kernel
+    sources and the constants of the C header), so that host-side changes to
+    the library keep a capture of unchanged kernels valid."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2412_14966_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in ("pv_device.cuh", "pv_kernels.cu", "pv_kernels.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     with open(os.path.join(ROOT, "include", "pv.h"), "rb") as fh:
-        h.update(fh.read())
+        h.update(b"".join(ln for ln in fh.readlines() if ln.startswith(b"#define")))
     return h.hexdigest()[:16]
 
 
