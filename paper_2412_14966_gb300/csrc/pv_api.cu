@@ -95,6 +95,7 @@ struct FusedLayout {
       first += cls_cap[c];
     }
     s.counters = reinterpret_cast<int*>(b + counter);
+    for (auto& c : s.stage) c = nullptr;
     return s;
   }
 };
@@ -219,6 +220,7 @@ struct pv_ctx {
   // 128-thread find CTAs, 256-thread fit CTAs, occupancy-sized grids)
   pvk::LaunchCfg bucket_cfg[3];
   int find_per_sm[4][4] = {};         // [mode][64/96/128/256]
+  int stage_per_sm[2] = {};           // staged find (kFindFitStaged) at 96/128 threads
   int fit_per_sm[3][2] = {};          // [accumulation mode][128/256]
   // CUDA graphs of the fused launch, keyed by its arguments
   std::map<std::string, cudaGraphExec_t> graphs;
@@ -498,6 +500,42 @@ int run_find_or_fit(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* see
   return enqueue_fused(ctx, mode, tracks, seeds, out, ctx->fused_ws.p, st);
 }
 
+// The device address of pinned host memory the device can reach, or NULL
+// (pageable memory, or a pointer CUDA does not know).
+void* device_alias(const void* hp) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, hp) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// The fused find + fit on tracks that live in host memory the device can
+// address: the find kernel reads them there and writes the device copy
+// `stage` (11 columns of n_tracks floats) that the fit kernel gathers from.
+int run_staged(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, float* const* stage,
+               cudaStream_t st) {
+  if (tracks->n_events == 0) return PV_OK;
+  FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
+  void* before = ctx->fused_ws.p;
+  PV_CUDA(ctx, ctx->fused_ws.ensure(L.total));
+  if (ctx->fused_ws.p != before) clear_graphs(ctx);   // graphs hold the old scratch
+  pvk::TrackScratch ws = L.scratch(ctx->fused_ws.p);
+  for (int c = 0; c < 11; ++c) ws.stage[c] = stage[c];
+  const pvk::LaunchCfg& b = ctx->bucket_cfg[bucket_of(tracks)];
+  const int nt = b.find_nt == 96 ? 96 : 128;
+  pvk::LaunchCfg cfg = launch_cfg(ctx, pvk::kFindFit, tracks, nt, b.fit_nt);
+  const int per = ctx->stage_per_sm[nt == 96 ? 0 : 1];
+  long long g = static_cast<long long>(ctx->n_sm) * (per > 0 ? per : 1);
+  cfg.find_grid = static_cast<int>(g < tracks->n_events ? g : tracks->n_events);
+  int nl = 0;
+  PV_CUDA(ctx, pvk::launch_fused(pvk::kFindFitStaged, ctx->C, track_ptrs(tracks), seed_ptrs(nullptr),
+                                 out_ptrs(out), ws, cfg, st, &nl));
+  ctx->launches += nl;
+  return PV_OK;
+}
+
 // ---- serving internals (ctx->mu held) ------------------------------------
 
 size_t request_bytes(const pv_tracks* t, const pv_vertices* o) {
@@ -647,6 +685,8 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
   for (int mode = 1; mode <= 3; ++mode)
     for (int i = 0; i < 4; ++i)
       ctx->find_per_sm[mode][i] = pvk::fused_blocks_per_sm(C.nbins, mode, nts[i], flav);
+  for (int i = 0; i < 2; ++i)
+    ctx->stage_per_sm[i] = pvk::fused_blocks_per_sm(C.nbins, pvk::kFindFitStaged, i ? 128 : 96, 0);
   for (int k = 0; k < 3; ++k)
     for (int i = 0; i < 2; ++i) ctx->fit_per_sm[k][i] = pvk::fit_blocks_per_sm(k, i == 0 ? 128 : 256);
   for (int b = 0; b < 3; ++b) ctx->bucket_cfg[b] = pvk::LaunchCfg{128, 0, pvk::kFitThreads, 0};
@@ -850,12 +890,24 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
       K = static_cast<int>(k < kRunHostChunks ? k : kRunHostChunks);
     }
   }
-  // device inputs: 11 float arrays + the chunks' offsets (E + K entries)
+  const float* src[11] = {h->x, h->y, h->z, h->tx, h->ty, h->cxx, h->cxtx, h->ctxtx,
+                          h->cyy, h->cyty, h->ctyty};
+  // On the fused path of the GPU flavour, tracks in pinned memory the device
+  // can address are read there by the find kernel itself, which writes the
+  // device copy the fit kernel gathers from: one pass over the host link and
+  // no input copies, so the batch runs as one chunk.
+  const float* alias[11] = {};
+  bool staged = ctx->cfg.path != PV_PATH_PLAIN && pvk::flavour_of(ctx->C) == 0 && n > 0;
+  for (int c = 0; c < 11 && staged; ++c) {
+    alias[c] = static_cast<const float*>(device_alias(src[c]));
+    staged = alias[c] != nullptr;
+  }
+  if (staged) K = 1;
+  // device inputs: 11 float arrays (copies of the host columns, or the staged
+  // find's device copy) + the chunks' offsets (E + K entries)
   size_t in_bytes = 11 * round16(4 * n) + round16(8 * (E + K));
   PV_CUDA(ctx, ctx->host_in.ensure(in_bytes));
   char* din = static_cast<char*>(ctx->host_in.p);
-  const float* src[11] = {h->x, h->y, h->z, h->tx, h->ty, h->cxx, h->cxtx, h->ctxtx,
-                          h->cyy, h->cyty, h->ctyty};
   float* dcol[11];
   for (int k = 0; k < 11; ++k) dcol[k] = reinterpret_cast<float*>(din + k * round16(4 * n));
   int64_t* doff = reinterpret_cast<int64_t*>(din + 11 * round16(4 * n));
@@ -873,15 +925,7 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
   size_t o = 0;
   auto plan = [&](void* hp, size_t elem, Unit u) -> int {
     if (!hp) return -1;
-    cudaPointerAttributes a{};
-    char* alias = nullptr;
-    if (!in_place) {
-      // staged
-    } else if (cudaPointerGetAttributes(&a, hp) == cudaSuccess) {
-      if (a.type == cudaMemoryTypeHost && a.devicePointer) alias = static_cast<char*>(a.devicePointer);
-    } else {
-      cudaGetLastError();   // not a pointer CUDA knows: stage it
-    }
+    char* alias = in_place ? static_cast<char*>(device_alias(hp)) : nullptr;
     const size_t count = u == kSlot ? static_cast<size_t>(E) * cap
                                     : (u == kEvent ? static_cast<size_t>(E)
                                                    : static_cast<size_t>(n));
@@ -927,9 +971,10 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
     cudaStream_t s_in = K > 1 ? ctx->rh_in : st;
     cudaStream_t s_out = K > 1 ? ctx->rh_out : st;
     const int64_t nt = b1 - b0;
-    for (int c = 0; c < 11; ++c)
-      if (nt) PV_CUDA(ctx, cudaMemcpyAsync(dcol[c] + b0, src[c] + b0, 4 * nt,
-                                           cudaMemcpyHostToDevice, s_in));
+    if (!staged)
+      for (int c = 0; c < 11; ++c)
+        if (nt) PV_CUDA(ctx, cudaMemcpyAsync(dcol[c] + b0, src[c] + b0, 4 * nt,
+                                             cudaMemcpyHostToDevice, s_in));
     // chunk k's offsets, relative to its first track, at entries e0 + k ..
     int64_t* doff_k = doff + e0 + k;
     if (K > 1) {
@@ -943,10 +988,11 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
       PV_CUDA(ctx, cudaMemcpyAsync(doff_k, hoff, 8 * (E + 1), cudaMemcpyHostToDevice, st));
     }
     pv_tracks dt = *h;
-    dt.x = dcol[0] + b0; dt.y = dcol[1] + b0; dt.z = dcol[2] + b0;
-    dt.tx = dcol[3] + b0; dt.ty = dcol[4] + b0;
-    dt.cxx = dcol[5] + b0; dt.cxtx = dcol[6] + b0; dt.ctxtx = dcol[7] + b0;
-    dt.cyy = dcol[8] + b0; dt.cyty = dcol[9] + b0; dt.ctyty = dcol[10] + b0;
+    const float* const* col = staged ? alias : const_cast<const float* const*>(dcol);
+    dt.x = col[0] + b0; dt.y = col[1] + b0; dt.z = col[2] + b0;
+    dt.tx = col[3] + b0; dt.ty = col[4] + b0;
+    dt.cxx = col[5] + b0; dt.cxtx = col[6] + b0; dt.ctxtx = col[7] + b0;
+    dt.cyy = col[8] + b0; dt.cyty = col[9] + b0; dt.ctyty = col[10] + b0;
     dt.event_offsets = doff_k;
     dt.n_tracks = nt;
     dt.n_events = static_cast<int32_t>(e1 - e0);
@@ -970,7 +1016,8 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
     dv.n_per_event = static_cast<int32_t*>(sp(inpe, e0));
     dv.event_status = static_cast<int32_t*>(sp(ievs, e0));
     dv.track_vertex = static_cast<int32_t*>(sp(itv, b0));
-    rc = run_find_or_fit(ctx, &dt, nullptr, &dv, st, pvk::kFindFit);
+    rc = staged ? run_staged(ctx, &dt, &dv, dcol, st)
+                : run_find_or_fit(ctx, &dt, nullptr, &dv, st, pvk::kFindFit);
     if (rc != PV_OK) return rc;
     if (K > 1) {
       PV_CUDA(ctx, cudaEventRecord(ctx->rh_ev[kRunHostChunks + k], st));

@@ -307,19 +307,32 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       // track per lane, then the warp's (track, bin) items spread over lanes)
       // the inputs of a warp's next 32 tracks are loaded while the current
       // ones are extrapolated and filled
+      // (kStage: the three y-covariance columns the fit needs are read too,
+      // and all eleven are written to the device copy)
       float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, r4 = 0.f, r5 = 0.f, r6 = 0.f, r7 = 0.f;
+      float r8 = 0.f, r9 = 0.f, r10 = 0.f;
       if (warp * 32 + lane < n) {
         const int64_t i = b0 + warp * 32 + lane;
         r0 = T.x[i]; r1 = T.y[i]; r2 = T.z[i]; r3 = T.tx[i];
         r4 = T.ty[i]; r5 = T.cxx[i]; r6 = T.cxtx[i]; r7 = T.ctxtx[i];
+        if constexpr ((MODE & kStage) != 0) { r8 = T.cyy[i]; r9 = T.cyty[i]; r10 = T.ctyty[i]; }
       }
       for (int t0 = warp * 32; t0 < n; t0 += NT) {
         const int t = t0 + lane;
         const float c0 = r0, c1 = r1, c2 = r2, c3 = r3, c4 = r4, c5 = r5, c6 = r6, c7 = r7;
+        if constexpr ((MODE & kStage) != 0) {
+          if (t < n) {
+            const int64_t i = b0 + t;
+            G.stage[0][i] = c0; G.stage[1][i] = c1; G.stage[2][i] = c2; G.stage[3][i] = c3;
+            G.stage[4][i] = c4; G.stage[5][i] = c5; G.stage[6][i] = c6; G.stage[7][i] = c7;
+            G.stage[8][i] = r8; G.stage[9][i] = r9; G.stage[10][i] = r10;
+          }
+        }
         if (t + NT < n) {
           const int64_t i = b0 + t + NT;
           r0 = T.x[i]; r1 = T.y[i]; r2 = T.z[i]; r3 = T.tx[i];
           r4 = T.ty[i]; r5 = T.cxx[i]; r6 = T.cxtx[i]; r7 = T.ctxtx[i];
+          if constexpr ((MODE & kStage) != 0) { r8 = T.cyy[i]; r9 = T.cyty[i]; r10 = T.ctyty[i]; }
         }
         Prep p;
         p.filled = false;
@@ -974,7 +987,10 @@ cudaError_t fused_setup(int nbins) {
   if ((err = setup_find_all<64>(nbins)) != cudaSuccess) return err;
   if ((err = setup_find_all<96>(nbins)) != cudaSuccess) return err;
   if ((err = setup_find_all<128>(nbins)) != cudaSuccess) return err;
-  return setup_find_all<256>(nbins);
+  if ((err = setup_find_all<256>(nbins)) != cudaSuccess) return err;
+  // the staged find (GPU flavour, 96- and 128-thread blocks)
+  if ((err = setup_find_flav<kFindFitStaged, 96, 0>(nbins)) != cudaSuccess) return err;
+  return setup_find_flav<kFindFitStaged, 128, 0>(nbins);
 }
 
 bool find_block_ok(int nt) { return nt == 64 || nt == 96 || nt == 128 || nt == 256; }
@@ -1004,6 +1020,8 @@ static int find_blocks_flav(int nbins, int flav) {
 }
 
 int fused_blocks_per_sm(int nbins, int mode, int nt, int flav) {
+  if (mode == kFindFitStaged)
+    return nt == 96 ? find_blocks<kFindFitStaged, 96>(nbins) : find_blocks<kFindFitStaged, 128>(nbins);
   if (flav != 0 && mode != kFit)
     return mode == kFind ? find_blocks_flav<kFind>(nbins, flav)
                          : find_blocks_flav<kFindFit>(nbins, flav);
@@ -1077,6 +1095,21 @@ cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const Se
   size_t sm = fused_smem_bytes(C.nbins, mode);
   cudaError_t err = cudaMemsetAsync(ws.counters, 0, kCounterInts * sizeof(int), st);
   if (err != cudaSuccess) return err;
+  if (mode == kFindFitStaged) {
+    // GPU flavour only; the fit gathers from the device copy
+    if (L.find_nt == 96)
+      find_kernel<kFindFitStaged, 96><<<L.find_grid, 96, sm, st>>>(C, T, S, O, ws);
+    else
+      find_kernel<kFindFitStaged, 128><<<L.find_grid, 128, sm, st>>>(C, T, S, O, ws);
+    TrackPtrs D = T;
+    D.x = ws.stage[0]; D.y = ws.stage[1]; D.z = ws.stage[2]; D.tx = ws.stage[3];
+    D.ty = ws.stage[4]; D.cxx = ws.stage[5]; D.cxtx = ws.stage[6]; D.ctxtx = ws.stage[7];
+    D.cyy = ws.stage[8]; D.cyty = ws.stage[9]; D.ctyty = ws.stage[10];
+    if (L.fit_nt == 128) launch_fit_ft<128>(C.accum_mode, L.fit_grid, st, C, D, ws, O);
+    else launch_fit_ft<256>(C.accum_mode, L.fit_grid, st, C, D, ws, O);
+    *n_launches += 2;
+    return cudaGetLastError();
+  }
   if (mode == kFind) launch_find<kFind>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
   else if (mode == kFit) launch_find<kFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
   else launch_find<kFindFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);

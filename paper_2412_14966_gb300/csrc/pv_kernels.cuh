@@ -67,6 +67,7 @@ struct TrackScratch {
   int cls_cap[kWorkClasses];    // its capacity
   int* counters;        // [0] next event, [1 + c] vertices listed in class c,
                         // [1 + kWorkClasses] next vertex to fit
+  float* stage[11];     // kStage: device copy of the 11 track columns (TrackPtrs order)
 };
 constexpr int kCounterInts = 8;
 
@@ -82,7 +83,11 @@ __host__ __device__ __forceinline__ V class_pick(const V (&a)[kWorkClasses], int
   return c == 0 ? a[0] : (c == 1 ? a[1] : (c == 2 ? a[2] : a[3]));
 }
 
-enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3 };
+enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3, kStage = 4 };
+// kFindFit | kStage: the tracks are in host memory the device can address; the
+// find kernel reads them there once and leaves a device copy (TrackScratch::
+// stage) that the fit kernel gathers from
+constexpr int kFindFitStaged = kFindFit | kStage;
 
 constexpr int kSmallCap = 256;      // tracks kept in shared memory per event
 constexpr int kFusedThreads = 128;

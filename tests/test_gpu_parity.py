@@ -375,7 +375,7 @@ def test_template_profile_flavour(pv, path, split):
 
 
 @pytest.mark.parametrize("case", ["nominal", "mixture", "unsplittable", "pageable", "plain",
-                                  "mixed"])
+                                  "mixed", "x86"])
 def test_run_host_pipeline_equals_device_path(pv, case):
     """pv_run_host splits batches of 4,096 events or more into event chunks
     whose copies overlap the kernels; the results equal the device path's bit
@@ -383,9 +383,11 @@ def test_run_host_pipeline_equals_device_path(pv, case):
     as one chunk and still matches (its bad event flagged the same way).
     Outputs in pinned memory are written in place, pageable ones (and all of
     the plain path's) are staged and copied back; "mixed" has both kinds in one
-    call."""
+    call.  Pinned inputs are read in place by the find kernel of the GPU
+    flavour, which leaves the device copy for the fit; pageable inputs, the
+    plain path and the x86 flavour copy them in by event chunks."""
     import torch
-    if case in ("nominal", "pageable", "plain", "mixed"):
+    if case in ("nominal", "pageable", "plain", "mixed", "x86"):
         batch = synthetic.workload_nominal(n_events=9000, seed=12)
     elif case == "mixture":
         batch = synthetic.workload_mixture(n_events=5000, seed=13)
@@ -394,7 +396,11 @@ def test_run_host_pipeline_equals_device_path(pv, case):
         off = batch.offsets.copy()
         off[-1] = off[-1] + 5            # the last event ends past the last track
         batch.offsets = off
-    cfg = dict(path=pv.PATH_PLAIN) if case == "plain" else dict(use_graph=1)
+    cfg = dict(use_graph=1)
+    if case == "plain":
+        cfg = dict(path=pv.PATH_PLAIN)
+    elif case == "x86":
+        cfg = dict(use_graph=1, split_mode=pv.SPLIT_RECURSIVE, profile_mode=pv.PROFILE_TEMPLATE)
     ctx = pv.Context(device=0, **cfg)
     s, v = G.gpu_find_fit(ctx, batch)
     host = pv.Tracks.from_host(batch, pinned=case != "pageable")
