@@ -564,8 +564,10 @@ def run_ours(args):
                                 "dip split (Sec. 3.2-3.3, x86 flavour)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "api": "pv_run_host (pinned host buffers; inputs copied in two event "
-                       "chunks, outputs written in place by the kernels)"},
+                "api": "pv_run_host (pinned host buffers: the find kernel reads 8 input "
+                       "columns in place and copies them to the device, the copy engine "
+                       "brings the other 3 beside it, outputs written in place by the "
+                       "kernels)"},
         "clocks": clk,
         "gpu_launches": launches,
     }

@@ -512,11 +512,23 @@ void* device_alias(const void* hp) {
 }
 
 // The fused find + fit on tracks that live in host memory the device can
-// address: the find kernel reads them there and writes the device copy
-// `stage` (11 columns of n_tracks floats) that the fit kernel gathers from.
+// address: the find kernel reads its eight columns there and writes them to
+// the device copy `stage` (11 columns of n_tracks floats) that the fit kernel
+// gathers from, while the copy engine brings the three y-covariance columns
+// (which only the fit reads) over the same link beside it.
 int run_staged(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, float* const* stage,
                cudaStream_t st) {
   if (tracks->n_events == 0) return PV_OK;
+  if (!ctx->rh_in) PV_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->rh_in, cudaStreamNonBlocking));
+  for (int i = 0; i < 2; ++i)
+    if (!ctx->rh_ev[i]) PV_CUDA(ctx, cudaEventCreateWithFlags(&ctx->rh_ev[i], cudaEventDisableTiming));
+  PV_CUDA(ctx, cudaEventRecord(ctx->rh_ev[0], st));
+  PV_CUDA(ctx, cudaStreamWaitEvent(ctx->rh_in, ctx->rh_ev[0], 0));
+  const float* ycol[3] = {tracks->cyy, tracks->cyty, tracks->ctyty};
+  for (int c = 0; c < 3; ++c)
+    PV_CUDA(ctx, cudaMemcpyAsync(stage[8 + c], ycol[c], 4 * tracks->n_tracks, cudaMemcpyDefault,
+                                 ctx->rh_in));
+  PV_CUDA(ctx, cudaEventRecord(ctx->rh_ev[1], ctx->rh_in));
   FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
   void* before = ctx->fused_ws.p;
   PV_CUDA(ctx, ctx->fused_ws.ensure(L.total));
@@ -531,7 +543,7 @@ int run_staged(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, float* co
   cfg.find_grid = static_cast<int>(g < tracks->n_events ? g : tracks->n_events);
   int nl = 0;
   PV_CUDA(ctx, pvk::launch_fused(pvk::kFindFitStaged, ctx->C, track_ptrs(tracks), seed_ptrs(nullptr),
-                                 out_ptrs(out), ws, cfg, st, &nl));
+                                 out_ptrs(out), ws, cfg, st, &nl, ctx->rh_ev[1]));
   ctx->launches += nl;
   return PV_OK;
 }

@@ -307,15 +307,13 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       // track per lane, then the warp's (track, bin) items spread over lanes)
       // the inputs of a warp's next 32 tracks are loaded while the current
       // ones are extrapolated and filled
-      // (kStage: the three y-covariance columns the fit needs are read too,
-      // and all eleven are written to the device copy)
+      // (kStage: the eight columns read here are also written to the device
+      // copy; the other three reach it by a copy alongside the kernel)
       float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, r4 = 0.f, r5 = 0.f, r6 = 0.f, r7 = 0.f;
-      float r8 = 0.f, r9 = 0.f, r10 = 0.f;
       if (warp * 32 + lane < n) {
         const int64_t i = b0 + warp * 32 + lane;
         r0 = T.x[i]; r1 = T.y[i]; r2 = T.z[i]; r3 = T.tx[i];
         r4 = T.ty[i]; r5 = T.cxx[i]; r6 = T.cxtx[i]; r7 = T.ctxtx[i];
-        if constexpr ((MODE & kStage) != 0) { r8 = T.cyy[i]; r9 = T.cyty[i]; r10 = T.ctyty[i]; }
       }
       for (int t0 = warp * 32; t0 < n; t0 += NT) {
         const int t = t0 + lane;
@@ -325,14 +323,12 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
             const int64_t i = b0 + t;
             G.stage[0][i] = c0; G.stage[1][i] = c1; G.stage[2][i] = c2; G.stage[3][i] = c3;
             G.stage[4][i] = c4; G.stage[5][i] = c5; G.stage[6][i] = c6; G.stage[7][i] = c7;
-            G.stage[8][i] = r8; G.stage[9][i] = r9; G.stage[10][i] = r10;
           }
         }
         if (t + NT < n) {
           const int64_t i = b0 + t + NT;
           r0 = T.x[i]; r1 = T.y[i]; r2 = T.z[i]; r3 = T.tx[i];
           r4 = T.ty[i]; r5 = T.cxx[i]; r6 = T.cxtx[i]; r7 = T.ctxtx[i];
-          if constexpr ((MODE & kStage) != 0) { r8 = T.cyy[i]; r9 = T.cyty[i]; r10 = T.ctyty[i]; }
         }
         Prep p;
         p.filled = false;
@@ -1091,7 +1087,7 @@ static void launch_find(int nt, int grid, size_t sm, cudaStream_t st, const Cons
 
 cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
                          const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
-                         cudaStream_t st, int* n_launches) {
+                         cudaStream_t st, int* n_launches, cudaEvent_t fit_after) {
   size_t sm = fused_smem_bytes(C.nbins, mode);
   cudaError_t err = cudaMemsetAsync(ws.counters, 0, kCounterInts * sizeof(int), st);
   if (err != cudaSuccess) return err;
@@ -1101,6 +1097,10 @@ cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const Se
       find_kernel<kFindFitStaged, 96><<<L.find_grid, 96, sm, st>>>(C, T, S, O, ws);
     else
       find_kernel<kFindFitStaged, 128><<<L.find_grid, 128, sm, st>>>(C, T, S, O, ws);
+    if (fit_after) {
+      err = cudaStreamWaitEvent(st, fit_after, 0);
+      if (err != cudaSuccess) return err;
+    }
     TrackPtrs D = T;
     D.x = ws.stage[0]; D.y = ws.stage[1]; D.z = ws.stage[2]; D.tx = ws.stage[3];
     D.ty = ws.stage[4]; D.cxx = ws.stage[5]; D.cxtx = ws.stage[6]; D.ctxtx = ws.stage[7];

@@ -85,8 +85,9 @@ __host__ __device__ __forceinline__ V class_pick(const V (&a)[kWorkClasses], int
 
 enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3, kStage = 4 };
 // kFindFit | kStage: the tracks are in host memory the device can address; the
-// find kernel reads them there once and leaves a device copy (TrackScratch::
-// stage) that the fit kernel gathers from
+// find kernel reads its eight columns there once and writes them to a device
+// copy (TrackScratch::stage) that the fit kernel gathers from; the other three
+// columns are copied in beside it
 constexpr int kFindFitStaged = kFindFit | kStage;
 
 constexpr int kSmallCap = 256;      // tracks kept in shared memory per event
@@ -142,10 +143,12 @@ struct LaunchCfg {
 };
 
 // Enqueues the fused path: counter reset, find kernel, then (modes with a fit)
-// the vertex fit kernel.  *n_launches receives the kernels enqueued.
+// the vertex fit kernel.  *n_launches receives the kernels enqueued.  In the
+// staged mode the fit kernel also waits for fit_after (if given): the copy of
+// the three columns the find kernel does not read.
 cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, const SeedPtrs& S,
                          const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
-                         cudaStream_t st, int* n_launches);
+                         cudaStream_t st, int* n_launches, cudaEvent_t fit_after = nullptr);
 
 // The checked build's record of out-of-bounds indices (count, first code),
 // reset by the call; false in the default build, which has no checks.
