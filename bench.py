@@ -448,6 +448,35 @@ def run_ours(args):
     pe.record(stream)
     torch.cuda.synchronize()
     plain_ms = ps.elapsed_time(pe) / plain_steps
+
+    # per-step device times of the plain path (the paper times each GPU step,
+    # Sec. 5): its entry points that stop after steps (a), (b) and (d1),
+    # differenced, and the fit alone from those seeds (the replicas hold the
+    # same batch, so one replica's seeds serve all)
+    def dev_ms(fn, n=50):
+        for i in range(2):
+            fn(i)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(n):
+            fn(i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    sd, fo = pv.Vertices.empty(E, NT, fit=False), pv.Vertices.empty(E, NT)
+    t_ext = dev_ms(lambda i: plain.extrapolate_batch(reps[i % N_REPLICAS], stream=stream))
+    t_hist = dev_ms(lambda i: plain.histogram_batch(reps[i % N_REPLICAS], stream=stream))
+    t_find = dev_ms(lambda i: plain.find_batch(reps[i % N_REPLICAS], out=sd, stream=stream))
+    plain.find_batch(reps[0], out=sd, stream=stream)
+    t_fit = dev_ms(lambda i: plain.fit_batch(reps[i % N_REPLICAS], sd, out=fo, stream=stream))
+    plain_stages = {"extrapolate": t_ext, "histogram": t_hist - t_ext,
+                    "peaks_and_association": t_find - t_hist, "fit": t_fit,
+                    "how": "CUDA events around 50 calls each of pv_extrapolate_batch, "
+                           "pv_histogram_batch, pv_find_batch and pv_fit_batch (given seeds) "
+                           "on the plain path, differenced"}
+    del sd, fo
     plain.close()
 
     # the GPU flavour of the fit (multi-vertex, Sec. 3.5): find + multi-vertex
@@ -554,7 +583,8 @@ def run_ours(args):
                      "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                      "kernel": "fused step: find_kernel<3> + fit_kernel<0> (one launch each)"},
         "plain": {"value": E * world / (plain_ms / 1e3), "ms_per_step": plain_ms,
-                  "path": "one kernel per step, global-memory histograms"},
+                  "path": "one kernel per step, global-memory histograms",
+                  "stages_ms": plain_stages},
         "multi": {"value": E * world / (multi_ms / 1e3), "ms_per_step": multi_ms,
                   "path": "find kernel + multi-vertex fit kernel (pv_fit_multi, GPU flavour "
                           "of the fit: implicit association, duplicate removal)"},

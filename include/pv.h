@@ -270,7 +270,7 @@ int pv_find_fit_static(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, v
 
 /* Project-written autotuner of the fused path's launch shape.  Runs the fused
  * find+fit on `sample` (device tracks) into `out` (device) with every
- * candidate pair of block sizes (find kernel 64/128/256 threads, fit kernel
+ * candidate pair of block sizes (find kernel 64/96/128/256 threads, fit kernel
  * 128/256), each with its occupancy-sized persistent grid, times them with
  * CUDA events on cuda_stream, and keeps the fastest for the sample's
  * event-size bucket (mean tracks per event below 300, below 800, 800 and

@@ -348,10 +348,11 @@ class Context:
                         stream=None) -> Vertices:
         """``pv_find_fit_static``: the fused find + fit with the library's
         static device scratch instead of allocated memory, for callers that
-        cannot allocate device memory while they run.  A batch needs 40 bytes
-        per track plus 32 per vertex slot within 8 MiB (about 155,000 tracks
-        of 160-track events); overlapping calls race (they share the
-        scratch)."""
+        cannot allocate device memory while they run.  A batch needs 31 bytes
+        per track plus 32 per entry of the four size-class vertex work lists
+        within 8 MiB (about 165,000 tracks of 160-track events at capacity 64;
+        larger batches get PV_ERR_CAPACITY); overlapping calls race (they
+        share the scratch)."""
         out = out or Vertices.empty(tracks.n_events, tracks.n_tracks)
         t, o = tracks.struct(), out.struct()
         self._check(self.lib.pv_find_fit_static(self.h, C.byref(t), C.byref(o),
