@@ -38,6 +38,7 @@ BYTES_PER_TRACK = 48     # 11 input floats + the track's vertex index
 BYTES_PER_VERTEX = 56    # position, covariance, chi2, ndof, counts, status
 BYTES_PER_EVENT = 8      # CSR offset
 N_REPLICAS = 4           # rotating input copies: 4 x 70 MB > 129 MB L2
+SERVE_SWEEP = (1e6, 5e6, 20e6, 30e6, 50e6)   # offered events/s of the serving sweep
 
 
 def _peaks():
@@ -268,7 +269,7 @@ def cpu_baseline(batch, max_seconds: float = 15.0) -> dict:
 
 
 def serving_run(pv, ctx, offered_hz: float, duration_s: float = 1.0, tick_s: float = 100e-6,
-                seed: int = 7) -> dict:
+                seed: int = 7, mix=None) -> dict:
     """Open-loop serving: events of the uneven mixture workload (mu ~ U(1, 12),
     20% fixed-target) arrive as a Poisson process at offered_hz; the events of
     each tick form one request, submitted with pv_submit and polled with
@@ -276,7 +277,8 @@ def serving_run(pv, ctx, offered_hz: float, duration_s: float = 1.0, tick_s: flo
     import torch
     from paper_2412_14966_gb300 import synthetic
     rng = np.random.default_rng(seed)
-    mix = synthetic.workload_mixture(n_events=20000, seed=seed)
+    if mix is None:
+        mix = synthetic.workload_mixture(n_events=20000, seed=seed)
     n_ticks = int(duration_s / tick_s)
     counts = rng.poisson(offered_hz * tick_s, size=n_ticks)
     # a ring of device request buffers, reused once their request is done
@@ -613,6 +615,15 @@ def run_ours(args):
         line["physics"]["pull_width"] = ph["pp"]["pull_width"]
     if args.serve_rate > 0:
         line["serving"] = serving_run(pv, ctx, args.serve_rate)
+        # offered-rate sweep (0.3 s each): where the served rate saturates and
+        # the latency grows
+        mix = synthetic.workload_mixture(n_events=20000, seed=7)
+        sweep = []
+        for rate in SERVE_SWEEP:
+            r = serving_run(pv, ctx, rate, duration_s=0.3, mix=mix)
+            sweep.append({k: r[k] for k in ("offered_events_per_s", "events_per_s", "p50_ms",
+                                            "p99_ms", "p999_ms", "requests")})
+        line["serving_sweep"] = sweep
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch)
     ctx.close()
