@@ -932,7 +932,9 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
   // and a copy back.
   const bool in_place = ctx->cfg.path != PV_PATH_PLAIN;
   enum Unit { kSlot, kEvent, kTrack };
-  struct Col { void* host; size_t elem; Unit unit; char* dev; bool direct; } cols[16];
+  // dev: where the kernels write the column (the host memory's device address,
+  // or the staging buffer at off once it is allocated)
+  struct Col { void* host; size_t elem; Unit unit; size_t off; char* dev; bool direct; } cols[16];
   int nc = 0;
   size_t o = 0;
   auto plan = [&](void* hp, size_t elem, Unit u) -> int {
@@ -941,7 +943,7 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
     const size_t count = u == kSlot ? static_cast<size_t>(E) * cap
                                     : (u == kEvent ? static_cast<size_t>(E)
                                                    : static_cast<size_t>(n));
-    cols[nc] = {hp, elem, u, alias ? alias : reinterpret_cast<char*>(o), alias != nullptr};
+    cols[nc] = {hp, elem, u, o, alias, alias != nullptr};
     if (!alias) o += round16(elem * count);
     return nc++;
   };
@@ -956,7 +958,7 @@ int pv_run_host(pv_ctx* ctx, const pv_tracks* h, pv_vertices* ho, void* stream) 
   PV_CUDA(ctx, ctx->host_out.ensure(o + 16));
   char* dout = static_cast<char*>(ctx->host_out.p);
   for (int c = 0; c < nc; ++c)
-    if (!cols[c].direct) cols[c].dev = dout + reinterpret_cast<size_t>(cols[c].dev);
+    if (!cols[c].direct) cols[c].dev = dout + cols[c].off;
 
   if (K > 1) {
     if (!ctx->rh_in)
