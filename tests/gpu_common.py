@@ -39,22 +39,26 @@ def gpu_find_fit(ctx, batch, fused=True, two_step=False):
 
 
 def assert_find_equal(gpu: dict, ref: dict, batch, events=None):
-    """Seeds, cluster bounds and track assignment: bit-exact."""
+    """Seeds, cluster bounds and track assignment: bit-exact, on every event
+    (or on ``events`` if given)."""
     E = batch.n_events
-    events = range(E) if events is None else events
     assert np.array_equal(gpu["n_per_event"][:E], ref["n"]), _first_diff(gpu["n_per_event"][:E], ref["n"])
     assert np.array_equal(gpu["event_status"][:E], ref["event_status"])
     tv = gpu["track_vertex"][:batch.n_tracks]
     assert np.array_equal(tv, ref["track_cluster"]), _first_diff(tv, ref["track_cluster"])
-    for e in events:
-        n = ref["n"][e]
-        for k, rk in (("bin_lo", "lo"), ("bin_hi", "hi"), ("bin_max", "bin")):
-            if k in gpu:
-                assert np.array_equal(gpu[k][e, :n], ref[rk][e, :n]), (e, k)
-        for k in ("x", "y", "z"):
-            g = np.ascontiguousarray(gpu[k][e, :n]).view(np.int32)
-            r = np.ascontiguousarray(ref[k][e, :n]).view(np.int32)
-            assert np.array_equal(g, r), (e, k, gpu[k][e, :n], ref[k][e, :n])
+    sel = np.arange(E) if events is None else np.asarray(list(events), dtype=np.int64)
+    K = ref["lo"].shape[1]
+    live = np.arange(K)[None, :] < ref["n"][sel][:, None]
+    for k, rk in (("bin_lo", "lo"), ("bin_hi", "hi"), ("bin_max", "bin")):
+        if k in gpu:
+            g = gpu[k][sel, :K]
+            bad = np.nonzero(live & (g != ref[rk][sel]))
+            assert len(bad[0]) == 0, (k, sel[bad[0][:5]], bad[1][:5])
+    for k in ("x", "y", "z"):
+        g = np.ascontiguousarray(gpu[k][sel, :K]).view(np.int32)
+        r = np.ascontiguousarray(ref[k][sel]).view(np.int32)
+        bad = np.nonzero(live & (g != r))
+        assert len(bad[0]) == 0, (k, sel[bad[0][:5]], bad[1][:5])
 
 
 def _first_diff(a, b):
@@ -63,11 +67,13 @@ def _first_diff(a, b):
 
 
 def fit_mismatches(gpu: dict, ref: dict, n_seeds: np.ndarray, cond=None):
-    """Per-vertex comparison.  Returns (list of (e, k) whose iteration counts
-    differ, dict of worst errors over vertices with equal counts).  A
-    covariance outside TOL_COV is accepted only for an ill-conditioned vertex
-    (``cond`` = (batch, found, params); see cov_spread) within ILL_FACTOR times
-    the oracle's own spread; those vertices are listed under "ill"."""
+    """Per-vertex comparison.  Returns (list of (e, k) to compare at the fixed
+    point, dict of worst errors over the others).  A vertex goes to the fixed
+    point when the paper's stopping rule did not decide it the same way on both
+    sides: the iteration counts differ, or both sides stopped at max_iter and
+    the covariance misses TOL_COV (a non-converged iterate).  A covariance
+    outside TOL_COV is otherwise accepted only for an ill-conditioned vertex
+    (see cov_ok); those are listed under "ill"."""
     worst = {"xy": 0.0, "z": 0.0, "cov": 0.0, "ill": []}
     differ = []
     for e in range(len(n_seeds)):
@@ -83,16 +89,36 @@ def fit_mismatches(gpu: dict, ref: dict, n_seeds: np.ndarray, cond=None):
             worst["xy"] = max(worst["xy"], abs(gpu["x"][e, k] - ref["x"][e, k]),
                               abs(gpu["y"][e, k] - ref["y"][e, k]))
             worst["z"] = max(worst["z"], abs(gpu["z"][e, k] - ref["z"][e, k]))
-            ce = cov_error(gpu["cov"][e, k], ref["cov"][e, k])
-            if ce >= TOL_COV and cond is not None:
-                spread = cov_spread(*cond, e, k)
-                assert spread >= TOL_COV / ILL_FACTOR and ce < ILL_FACTOR * spread, (e, k, ce, spread)
-                worst["ill"].append((e, k, ce, spread))
-            else:
-                worst["cov"] = max(worst["cov"], ce)
             assert gs == rs, (e, k, gs, rs, gpu["n_tracks"][e, k], ref["n_tracks"][e, k])
             assert gpu["n_tracks"][e, k] == ref["n_tracks"][e, k], (e, k)
+            ce = cov_error(gpu["cov"][e, k], ref["cov"][e, k])
+            if ce < TOL_COV:
+                worst["cov"] = max(worst["cov"], ce)
+            elif rs & oracle.MAXITER:
+                differ.append((e, k))
+            else:
+                worst["ill"].append(cov_ok(ce, rs, cond, e, k, "paper rule"))
     return differ, worst
+
+
+def cov_ok(ce: float, status: int, cond, e: int, k: int, where: str):
+    """The one exception to TOL_COV: an ill-conditioned covariance, one whose
+    oracle value moves by at least TOL_COV / ILL_FACTOR when the vertex's
+    binary32 track inputs move by one ulp (see cov_spread), may differ by up to
+    ILL_FACTOR times that spread, and never by ILL_CAP or more.  A primary
+    vertex of the final selection (status ACCEPTED) gets it only when the
+    oracle's own one-ulp spread is at least TOL_COV: the tolerance is then
+    finer than what its binary32 inputs determine.  Returns the vertex's record
+    for the test's report."""
+    assert cond is not None, ("covariance outside tolerance", where, e, k, ce)
+    spread = cov_spread(*cond, e, k)
+    assert spread >= TOL_COV / ILL_FACTOR, ("not ill-conditioned", where, e, k, ce, spread)
+    if status & oracle.ACCEPTED:
+        assert spread >= TOL_COV, ("accepted PV outside TOL_COV", where, e, k, ce, spread, status)
+    assert ce < min(ILL_FACTOR * spread, ILL_CAP), ("beyond the cap", where, e, k, ce, spread)
+    batch, found = cond[0], cond[1]
+    ntrk = int(vertex_tracks(batch, found, e, k)["x"].shape[0])
+    return (where, int(e), int(k), float(ce), float(spread), ntrk, int(status))
 
 
 def cov_error(g, r) -> float:
@@ -111,6 +137,8 @@ def cov_error(g, r) -> float:
 # carries most of the z information, is the typical case); it is compared at
 # ILL_FACTOR times that spread instead.
 ILL_FACTOR = 10.0
+# and whatever the spread, an exempted covariance stays within 1e-3
+ILL_CAP = 1e-3
 
 
 def vertex_tracks(batch, found: dict, e: int, k: int) -> dict:
@@ -143,18 +171,19 @@ def cov_spread(batch, found: dict, p, e: int, k: int, n_draw: int = 8) -> float:
 
 
 def assert_fit_close(gpu, ref, n_seeds, tight_pair=None, cond=None):
-    """Tolerances on every vertex whose iteration counts agree; the others are
-    refitted on both sides to full convergence (``tight_pair`` = callable
-    returning (gpu_tight, ref_tight)) and compared there.  ``cond`` =
-    (batch, found, params) enables the ill-conditioned rule of
-    fit_mismatches."""
+    """Tolerances on every vertex the paper's stopping rule decided alike on
+    both sides; the others (iteration counts differ, or both stopped at
+    max_iter with the covariance outside TOL_COV) are refitted on both sides to
+    full convergence (``tight_pair`` = callable returning (gpu_tight,
+    ref_tight)) and compared there.  ``cond`` = (batch, found, params) enables
+    the ill-conditioned rule of cov_ok."""
     differ, worst = fit_mismatches(gpu, ref, n_seeds, cond)
     assert worst["xy"] < TOL_XY, worst
     assert worst["z"] < TOL_Z, worst
     assert worst["cov"] < TOL_COV, worst
     n_total = int(np.sum(n_seeds))
     if differ:
-        assert tight_pair is not None, f"{len(differ)} iteration-count mismatches"
+        assert tight_pair is not None, f"{len(differ)} vertices to compare at the fixed point"
         # fixed points are compared where the paper's stopping rule was not decisive
         assert len(differ) <= max(3, 0.05 * n_total), (len(differ), n_total)
         gt, rt = tight_pair()
@@ -162,8 +191,27 @@ def assert_fit_close(gpu, ref, n_seeds, tight_pair=None, cond=None):
             assert abs(gt["x"][e, k] - rt["x"][e, k]) < TOL_XY, (e, k)
             assert abs(gt["y"][e, k] - rt["y"][e, k]) < TOL_XY, (e, k)
             assert abs(gt["z"][e, k] - rt["z"][e, k]) < TOL_Z, (e, k)
-            assert cov_error(gt["cov"][e, k], rt["cov"][e, k]) < TOL_COV, (e, k)
+            ce = cov_error(gt["cov"][e, k], rt["cov"][e, k])
+            if ce >= TOL_COV:
+                worst["ill"].append(cov_ok(ce, int(rt["status"][e, k]), cond, e, k, "fixed point"))
     return worst, len(differ)
+
+
+def tight_refit(pv, batch, seeds_np, found_ref, beam=(0.0, 0.0, 0.0, 0.0), **cfg):
+    """Both sides refitted from the same seeds to full convergence (|dz| <
+    0.01 um, |dchi2| < 1e-4, at most 60 iterations)."""
+    import torch
+    kw = dict(dz_tol=1e-5, dchi2_tol=1e-4, max_iter=60)
+    ctx = pv.Context(device=0, beamline=beam, **cfg, **kw)
+    tracks = pv.Tracks.from_batch(batch)
+    seeds = pv.Vertices({k: torch.from_numpy(v).cuda() for k, v in seeds_np.items()}, 64)
+    out = ctx.fit_batch(tracks, seeds)
+    torch.cuda.synchronize()
+    g = out.numpy()
+    ctx.close()
+    p = oracle_params_for(beam=beam, **kw)
+    r = oracle.fit_batch(batch, found_ref, p)
+    return g, r
 
 
 def _ulp_moved(t: dict, rng) -> dict:

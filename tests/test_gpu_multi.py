@@ -8,12 +8,13 @@ iterations.  Every other vertex (rejected candidates and duplicates, whose
 soft weights make the fit's path and its last-iteration weights sensitive to
 rounding) is compared at the method's fixed point: both sides refit from the
 same seeds until they no longer move, and positions and covariances meet the
-tolerances there, except ill-conditioned ones (the oracle's own result moves
-by more than a tenth of a tolerance under one-ulp input changes: compared at
-ten times that spread) and degenerate ones (sigma_z above 1 mm: checked to be
-finite).  Track counts (weights against 0.5), per-track vertices (largest
-weight) and duplicate and selection decisions are integers decided by binary32
-and binary64 weights; they must agree on all but a few vertices and tracks."""
+tolerances there.  The comparison knows two exceptions (ill-conditioned
+vertices, compared at ten times the oracle's own one-ulp spread and never
+beyond 1e-3 on the covariance, and degenerate ones with sigma_z above 1 mm);
+no vertex of the tested batches needs either, and the test asserts that.
+Track counts (weights against 0.5), per-track vertices (largest weight) and
+the duplicate and selection decisions are integers decided by binary32 and
+binary64 weights; they are identical to the oracle's on every tested batch."""
 import numpy as np
 import pytest
 
@@ -101,7 +102,9 @@ def _compare(pv, batch, g, ref, fit, p=None):
             for err, tol, spr in ((dxy[e, k], G.TOL_XY, sxy), (dz[e, k], G.TOL_Z, sz),
                                   (ce, G.TOL_COV, sc)):
                 assert err < tol or (spr >= tol / F and err < F * spr), (where, e, k, err, tol, spr)
-            special.append(("ill-conditioned", where, int(e), int(k)))
+            assert ce < G.ILL_CAP, (where, e, k, ce)
+            special.append(("ill-conditioned", where, int(e), int(k), int(rr["status"][e, k]),
+                            float(dxy[e, k]), float(dz[e, k]), float(ce)))
         return special
 
     special = check(g, fit, accepted, "paper rule")
@@ -122,18 +125,21 @@ def _compare(pv, batch, g, ref, fit, p=None):
         assert int(srest.sum()) - int(fixed.sum()) <= max(3, 2e-3 * n_ok), \
             (int(srest.sum()), int(fixed.sum()))
         special += check_sub(gt, rt, fixed, sub, sref)
-    assert len(special) <= max(3, 2e-3 * n_ok), special
-    # integers decided by floating point
+    # none on the tested batches
+    assert not special, special
+    # integers decided by floating point: identical to the oracle's
     dn = np.abs(g["n_tracks"][:E, :K].astype(int) - fit["n_tracks"])[same_it]
-    assert dn.max(initial=0) <= 1 and np.mean(dn != 0) <= 0.01, (dn.max(initial=0), np.mean(dn != 0))
-    tv_agree = np.mean(g["track_vertex"][:batch.n_tracks] == fit["track_vertex"])
-    assert tv_agree >= 0.999, tv_agree
+    assert not dn.any(), ("n_tracks differ", int((dn != 0).sum()))
+    tv_g = g["track_vertex"][:batch.n_tracks]
+    tv_agree = np.mean(tv_g == fit["track_vertex"])
+    assert np.array_equal(tv_g, fit["track_vertex"]), \
+        ("track_vertex differs", int(np.sum(tv_g != fit["track_vertex"])))
     dup_g = (gs & oracle.DUPLICATE) != 0
     dup_r = (rs & oracle.DUPLICATE) != 0
-    assert np.mean(dup_g[ok] != dup_r[ok]) <= 0.01
+    assert np.array_equal(dup_g[ok], dup_r[ok]), ("duplicate sets differ", int(np.sum(dup_g[ok] != dup_r[ok])))
     acc_g = (gs & oracle.ACCEPTED) != 0
     acc_r = (rs & oracle.ACCEPTED) != 0
-    assert np.mean(acc_g[ok] != acc_r[ok]) <= 0.01
+    assert np.array_equal(acc_g[ok], acc_r[ok]), ("accepted sets differ", int(np.sum(acc_g[ok] != acc_r[ok])))
     return {"vertices": n_ok, "accepted_same_iter": int(accepted.sum()),
             "fixed_point_compared": int(fixed.sum()), "special": special,
             "n_tracks_differ": int((dn != 0).sum()), "track_vertex_agree": float(tv_agree),
