@@ -52,16 +52,20 @@ def _peaks():
 
 
 def _sources_hash() -> str:
-    """Hash of the device code the fused kernels are built from (the kernel
-    sources and the constants of the C header), so that host-side changes to
-    the library keep a capture of unchanged kernels valid."""
+    """Hash of what the fused kernels' DRAM traffic depends on: every CUDA
+    source of the library (kernels, and the host code that lays out the
+    scratch and sizes the grids), the constants of the C header and the nvcc
+    flags of the build; header comments do not enter it."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2412_14966_gb300", "csrc")
-    for f in ("pv_device.cuh", "pv_kernels.cu", "pv_kernels.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
     with open(os.path.join(ROOT, "include", "pv.h"), "rb") as fh:
         h.update(b"".join(ln for ln in fh.readlines() if ln.startswith(b"#define")))
+    from paper_2412_14966_gb300 import build as _b
+    h.update(" ".join(f for f in _b.ARCH + _b.NVCC_FLAGS if not os.path.isabs(f)).encode())
     return h.hexdigest()[:16]
 
 

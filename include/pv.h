@@ -16,6 +16,13 @@
  *     memory, CUDA graphs and serving state.
  *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Device work is enqueued asynchronously on it unless stated.
+ *     The context keeps one set of scratch memory per stream it has seen, so
+ *     calls on different streams may overlap on the GPU; calls on one stream
+ *     run in stream order.  pv_find_fit_static is the exception (one static
+ *     scratch array for all calls, see there).
+ *   - A context is not thread-safe: calls from several host threads on one
+ *     context must be serialised by the caller, except pv_submit, pv_poll and
+ *     pv_request_latency_ns, which lock the context's serving state.
  *   - Per-event and per-track problems are reported in the outputs (event and
  *     vertex status words, track_vertex = -1), not as errors: a non-finite
  *     track is simply not used.
@@ -261,7 +268,9 @@ int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns);
  * events x out->capacity: about 165,000 tracks of 160-track events at
  * capacity 64.  Batches needing more are refused with PV_ERR_CAPACITY and a
  * message in pv_last_cuda_error.  The first call on a device looks the array up
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  The
+ * address is kept for the life of the process: it assumes the device's primary
+ * context lives as long (do not call this entry point after cudaDeviceReset).
  * All calls share the array, so calls whose work overlaps on the GPU race:
  * run them on one stream or order them with events.  tracks and out are
  * device memory as for pv_fit_batch; the context's path setting is ignored
@@ -297,6 +306,11 @@ const char* pv_last_cuda_error(const pv_ctx* ctx);
 /* Number of kernel launches the library enqueued since the context was
  * created (all entry points); used to count launches in a timed region. */
 uint64_t pv_launch_count(const pv_ctx* ctx);
+
+/* Device memory the context holds (scratch of every stream it has seen, the
+ * template table, pv_run_host's staging and the serving pool), in bytes; 0
+ * for NULL.  Grows only when an entry point needs more. */
+uint64_t pv_device_bytes(const pv_ctx* ctx);
 
 #ifdef __cplusplus
 }

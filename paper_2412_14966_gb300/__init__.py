@@ -36,7 +36,7 @@ EXPORTED = (
     "pv_extrapolate_batch", "pv_histogram_batch", "pv_num_bins", "pv_run_host", "pv_submit",
     "pv_poll", "pv_request_latency_ns", "pv_strerror", "pv_last_cuda_error", "pv_launch_count",
     "pv_find_fit_static", "pv_autotune", "pv_launch_config", "pv_set_launch_config",
-    "pv_fit_multi", "pv_check_report",
+    "pv_fit_multi", "pv_check_report", "pv_device_bytes",
 )
 
 
@@ -129,6 +129,8 @@ def load():
     L.pv_last_cuda_error.restype = C.c_char_p
     L.pv_launch_count.argtypes = [C.c_void_p]
     L.pv_launch_count.restype = C.c_uint64
+    L.pv_device_bytes.argtypes = [C.c_void_p]
+    L.pv_device_bytes.restype = C.c_uint64
     L.pv_find_fit_static.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
     L.pv_autotune.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
     L.pv_set_launch_config.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
@@ -296,6 +298,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.pv_launch_count(self.h))
+
+    def device_bytes(self) -> int:
+        """``pv_device_bytes``: device memory the context holds."""
+        return int(self.lib.pv_device_bytes(self.h))
 
     # -- device entry points --------------------------------------------------
     def find_batch(self, tracks: Tracks, out: Vertices | None = None, stream=None) -> Vertices:

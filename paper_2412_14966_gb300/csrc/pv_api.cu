@@ -60,7 +60,7 @@ size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
 // Carves fused-path scratch for a batch out of one buffer.
 struct FusedLayout {
-  size_t counter, center, cid, sorted, A, W, work, total;
+  size_t counter, center, cid, slot, A, W, work, total;
   int64_t work_cap;
   int64_t cls_cap[pvk::kWorkClasses];
   FusedLayout(int64_t n, int64_t n_events, int cap) {
@@ -75,7 +75,7 @@ struct FusedLayout {
     W = o; o += round16(sizeof(float2) * n);
     center = o; o += round16(sizeof(int16_t) * n);
     cid = o; o += round16(sizeof(int8_t) * n);
-    sorted = o; o += round16(sizeof(int32_t) * n);
+    slot = o; o += round16(sizeof(int32_t) * n);
     work = o; o += round16(sizeof(pvk::VertexWork) * work_cap);
     total = o;
   }
@@ -84,7 +84,7 @@ struct FusedLayout {
     pvk::TrackScratch s;
     s.center = reinterpret_cast<int16_t*>(b + center);
     s.cid = reinterpret_cast<int8_t*>(b + cid);
-    s.sorted = reinterpret_cast<int32_t*>(b + sorted);
+    s.slot = reinterpret_cast<int32_t*>(b + slot);
     s.A = reinterpret_cast<float4*>(b + A);
     s.W = reinterpret_cast<float2*>(b + W);
     s.work = reinterpret_cast<pvk::VertexWork*>(b + work);
@@ -225,7 +225,12 @@ struct pv_ctx {
   // CUDA graphs of the fused launch, keyed by its arguments
   std::map<std::string, cudaGraphExec_t> graphs;
   cudaStream_t capture_stream = nullptr;
-  DevBuf fused_ws, plain_ws, mv_ws;
+  // scratch of the device entry points, one set per CUDA stream, so that calls
+  // on different streams may overlap on the GPU
+  struct StreamWs {
+    DevBuf fused, plain, mv;
+  };
+  std::map<cudaStream_t, StreamWs> ws;
   DevBuf tpl;                         // template profiles (profile_mode TEMPLATE)
   int mv_per_sm = 0;
   // host-buffer entry point staging
@@ -477,8 +482,9 @@ int run_find_or_fit(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* see
   if (tracks->n_events == 0) return PV_OK;
   if (ctx->cfg.path == PV_PATH_PLAIN) {
     PlainLayout L(tracks->n_tracks, tracks->n_events, ctx->C.nbins);
-    PV_CUDA(ctx, ctx->plain_ws.ensure(L.total));
-    pvk::PlainScratch ws = L.scratch(ctx->plain_ws.p);
+    DevBuf& pbuf = ctx->ws[st].plain;
+    PV_CUDA(ctx, pbuf.ensure(L.total));
+    pvk::PlainScratch ws = L.scratch(pbuf.p);
     int n = 0;
     pvk::TrackPtrs T = track_ptrs(tracks);
     if (mode & pvk::kFind) {
@@ -492,12 +498,13 @@ int run_find_or_fit(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* see
     return PV_OK;
   }
   FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
-  void* before = ctx->fused_ws.p;
-  PV_CUDA(ctx, ctx->fused_ws.ensure(L.total));
-  if (ctx->fused_ws.p != before) clear_graphs(ctx);   // graphs hold the old scratch
+  DevBuf& fbuf = ctx->ws[st].fused;
+  void* before = fbuf.p;
+  PV_CUDA(ctx, fbuf.ensure(L.total));
+  if (fbuf.p != before) clear_graphs(ctx);   // graphs hold the old scratch
   if (ctx->cfg.use_graph && mode == pvk::kFindFit)
-    return enqueue_fused_graph(ctx, tracks, out, ctx->fused_ws.p, st);
-  return enqueue_fused(ctx, mode, tracks, seeds, out, ctx->fused_ws.p, st);
+    return enqueue_fused_graph(ctx, tracks, out, fbuf.p, st);
+  return enqueue_fused(ctx, mode, tracks, seeds, out, fbuf.p, st);
 }
 
 // The device address of pinned host memory the device can reach, or NULL
@@ -512,29 +519,20 @@ void* device_alias(const void* hp) {
 }
 
 // The fused find + fit on tracks that live in host memory the device can
-// address: the find kernel reads its eight columns there and writes them to
-// the device copy `stage` (11 columns of n_tracks floats) that the fit kernel
-// gathers from, while the copy engine brings the three y-covariance columns
-// (which only the fit reads) over the same link beside it.
+// address: the find kernel reads every column there once (the eight of steps
+// (a)-(b) in its fill, writing them to the device copy `stage` (8 columns of
+// n_tracks floats) that its fit-input pass reads back, the other three in
+// that pass).
 int run_staged(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, float* const* stage,
                cudaStream_t st) {
   if (tracks->n_events == 0) return PV_OK;
-  if (!ctx->rh_in) PV_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->rh_in, cudaStreamNonBlocking));
-  for (int i = 0; i < 2; ++i)
-    if (!ctx->rh_ev[i]) PV_CUDA(ctx, cudaEventCreateWithFlags(&ctx->rh_ev[i], cudaEventDisableTiming));
-  PV_CUDA(ctx, cudaEventRecord(ctx->rh_ev[0], st));
-  PV_CUDA(ctx, cudaStreamWaitEvent(ctx->rh_in, ctx->rh_ev[0], 0));
-  const float* ycol[3] = {tracks->cyy, tracks->cyty, tracks->ctyty};
-  for (int c = 0; c < 3; ++c)
-    PV_CUDA(ctx, cudaMemcpyAsync(stage[8 + c], ycol[c], 4 * tracks->n_tracks, cudaMemcpyDefault,
-                                 ctx->rh_in));
-  PV_CUDA(ctx, cudaEventRecord(ctx->rh_ev[1], ctx->rh_in));
   FusedLayout L(tracks->n_tracks, tracks->n_events, out->capacity);
-  void* before = ctx->fused_ws.p;
-  PV_CUDA(ctx, ctx->fused_ws.ensure(L.total));
-  if (ctx->fused_ws.p != before) clear_graphs(ctx);   // graphs hold the old scratch
-  pvk::TrackScratch ws = L.scratch(ctx->fused_ws.p);
-  for (int c = 0; c < 11; ++c) ws.stage[c] = stage[c];
+  DevBuf& fbuf = ctx->ws[st].fused;
+  void* before = fbuf.p;
+  PV_CUDA(ctx, fbuf.ensure(L.total));
+  if (fbuf.p != before) clear_graphs(ctx);   // graphs hold the old scratch
+  pvk::TrackScratch ws = L.scratch(fbuf.p);
+  for (int c = 0; c < 8; ++c) ws.stage[c] = stage[c];
   const pvk::LaunchCfg& b = ctx->bucket_cfg[bucket_of(tracks)];
   const int nt = b.find_nt == 96 ? 96 : 128;
   pvk::LaunchCfg cfg = launch_cfg(ctx, pvk::kFindFit, tracks, nt, b.fit_nt);
@@ -543,7 +541,7 @@ int run_staged(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, float* co
   cfg.find_grid = static_cast<int>(g < tracks->n_events ? g : tracks->n_events);
   int nl = 0;
   PV_CUDA(ctx, pvk::launch_fused(pvk::kFindFitStaged, ctx->C, track_ptrs(tracks), seed_ptrs(nullptr),
-                                 out_ptrs(out), ws, cfg, st, &nl, ctx->rh_ev[1]));
+                                 out_ptrs(out), ws, cfg, st, &nl));
   ctx->launches += nl;
   return PV_OK;
 }
@@ -735,9 +733,12 @@ int pv_destroy(pv_ctx* ctx) {
   cudaDeviceSynchronize();
   clear_graphs(ctx);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-  ctx->fused_ws.release();
-  ctx->plain_ws.release();
-  ctx->mv_ws.release();
+  for (auto& kv : ctx->ws) {
+    kv.second.fused.release();
+    kv.second.plain.release();
+    kv.second.mv.release();
+  }
+  ctx->ws.clear();
   ctx->tpl.release();
   ctx->host_in.release();
   ctx->host_out.release();
@@ -826,8 +827,9 @@ int pv_fit_multi(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
   const size_t o_vczz = o; o += round16(sizeof(float) * slots);
   const size_t o_vn = o; o += round16(sizeof(int) * slots);
   const size_t o_vst = o; o += round16(sizeof(int) * slots);
-  PV_CUDA(ctx, ctx->mv_ws.ensure(o));
-  char* base = static_cast<char*>(ctx->mv_ws.p);
+  DevBuf& mbuf = ctx->ws[st].mv;
+  PV_CUDA(ctx, mbuf.ensure(o));
+  char* base = static_cast<char*>(mbuf.p);
   pvk::MvScratch M;
   M.counters = reinterpret_cast<int*>(base + o_cnt);
   M.K = reinterpret_cast<int*>(base + o_K);
@@ -869,9 +871,10 @@ int pv_histogram_batch(pv_ctx* ctx, const pv_tracks* tracks, uint32_t* hist, voi
   cudaSetDevice(ctx->device);
   if (tracks->n_events == 0) return PV_OK;
   PlainLayout L(tracks->n_tracks, 0, ctx->C.nbins);
-  PV_CUDA(ctx, ctx->plain_ws.ensure(L.total));
+  DevBuf& pbuf = ctx->ws[static_cast<cudaStream_t>(stream)].plain;
+  PV_CUDA(ctx, pbuf.ensure(L.total));
   int n = 0;
-  PV_CUDA(ctx, pvk::launch_histogram(ctx->C, track_ptrs(tracks), hist, L.scratch(ctx->plain_ws.p),
+  PV_CUDA(ctx, pvk::launch_histogram(ctx->C, track_ptrs(tracks), hist, L.scratch(pbuf.p),
                                      static_cast<cudaStream_t>(stream), &n));
   ctx->launches += n;
   return PV_OK;
@@ -1135,6 +1138,13 @@ const char* pv_last_cuda_error(const pv_ctx* ctx) { return ctx ? ctx->last_error
 
 uint64_t pv_launch_count(const pv_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
+uint64_t pv_device_bytes(const pv_ctx* ctx) {
+  if (!ctx) return 0;
+  uint64_t b = ctx->tpl.bytes + ctx->host_in.bytes + ctx->host_out.bytes + ctx->pool.bytes;
+  for (const auto& kv : ctx->ws) b += kv.second.fused.bytes + kv.second.plain.bytes + kv.second.mv.bytes;
+  return b;
+}
+
 }  // extern "C"
 
 // ===========================================================================
@@ -1149,8 +1159,10 @@ uint64_t pv_launch_count(const pv_ctx* ctx) { return ctx ? ctx->launches.load() 
 // GPU that loads this library holds until the process exits.  Host code only
 // ever passes the array's device address, obtained with cudaGetSymbolAddress
 // once per device (the array's name is a host-side stand-in, not a device
-// address).  Calls share the array: two calls whose work overlaps on the GPU
-// race, so callers serialise them (one stream, or events between streams).
+// address) and kept for the life of the process, which assumes the device's
+// primary context lives as long.  Calls share the array: two calls whose work
+// overlaps on the GPU race, so callers serialise them (one stream, or events
+// between streams).
 
 namespace {
 
@@ -1195,7 +1207,7 @@ extern "C" int pv_find_fit_static(pv_ctx* ctx, const pv_tracks* tracks, pv_verti
     ctx->last_error = msg;
     return PV_ERR_CAPACITY;
   }
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return PV_ERR_CUDA;
+  PV_CUDA(ctx, cudaSetDevice(ctx->device));
   void* base = nullptr;
   rc = static_scratch_for(ctx, &base);
   if (rc != PV_OK) return rc;
@@ -1226,9 +1238,10 @@ extern "C" int pv_autotune(pv_ctx* ctx, const pv_tracks* sample, pv_vertices* ou
   cudaSetDevice(ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   FusedLayout FL(sample->n_tracks, sample->n_events, out->capacity);
-  void* before = ctx->fused_ws.p;
-  PV_CUDA(ctx, ctx->fused_ws.ensure(FL.total));
-  if (ctx->fused_ws.p != before) clear_graphs(ctx);
+  DevBuf& fbuf = ctx->ws[st].fused;
+  void* before = fbuf.p;
+  PV_CUDA(ctx, fbuf.ensure(FL.total));
+  if (fbuf.p != before) clear_graphs(ctx);
   cudaEvent_t e0, e1;
   PV_CUDA(ctx, cudaEventCreate(&e0));
   PV_CUDA(ctx, cudaEventCreate(&e1));
@@ -1242,7 +1255,7 @@ extern "C" int pv_autotune(pv_ctx* ctx, const pv_tracks* sample, pv_vertices* ou
       float t_min = -1.f;
       for (int rep = 0; rep < 4; ++rep) {
         PV_CUDA(ctx, cudaEventRecord(e0, st));
-        rc = enqueue_fused_cfg(ctx, pvk::kFindFit, sample, nullptr, out, ctx->fused_ws.p, cfg, st);
+        rc = enqueue_fused_cfg(ctx, pvk::kFindFit, sample, nullptr, out, fbuf.p, cfg, st);
         if (rc != PV_OK) return rc;
         PV_CUDA(ctx, cudaEventRecord(e1, st));
         PV_CUDA(ctx, cudaEventSynchronize(e1));

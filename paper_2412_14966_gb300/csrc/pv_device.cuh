@@ -100,6 +100,11 @@ __device__ __forceinline__ int tpl_class(float sigma, const TplTable* t) {
   return lo;
 }
 
+// Brings the 128-byte line holding *p into L2 (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // ---------------------------------------------------------------------------
 // step (a): extrapolation, Eq. zpocadef, Eq. Vxy (diagonal block), sigma_poca
 
@@ -224,21 +229,36 @@ __device__ __forceinline__ void fill_template(uint32_t* hist, int tq, int j0, in
 }
 
 // Warp-cooperative fill of the profiles of the 32 tracks held by the lanes
-// (one per lane; nb = 0 for a lane without a filled track).  The warp's
-// (track, bin) items are spread over the lanes, so no lane idles while
-// another walks a long window.  Bin j of a window [j0, j1] receives
-// Q_{j+1} - Q_j with Q_{j0} = 0, Q_{j1+1} = ONE and Q_j the quantised CDF at
-// edge j: each lane evaluates the CDF at the left edge of its bin and takes
-// the right edge from the next lane (items of one track sit in consecutive
-// lanes), so a pass covers 31 items and lane 31 only supplies an edge.  The
-// running-max guard of fill_profile is a no-op that is not repeated here: Q is
-// non-decreasing along a window because F is monotone on [-1, 1], every
-// binary32 step of u and F is a monotone rounding, and window edges are at
-// least dz / (sqrt(5) sigma_max) = 0.011 apart in u, far above the rounding
-// error of F.  The histogram is therefore the one fill_profile builds.  With
-// kProfile = TEMPLATE the left-edge value is the class template's Q[i] (tq:
-// the class's start in q) instead of the CDF, and the histogram is the one
-// fill_template builds.
+// (one per lane; nb = 0 for a lane without a filled track).  Bin j0 + i of a
+// window [j0, j0 + nb) receives Q_{i+1} - Q_i with Q_0 = 0, Q_nb = ONE and Q_i
+// the quantised CDF at the bin edge j0 + i.  The running-max guard of
+// fill_profile is a no-op that is not repeated here: Q is non-decreasing along
+// a window because F is monotone on [-1, 1], every binary32 step of u and F is
+// a monotone rounding, and window edges are at least dz / (sqrt(5) sigma_max)
+// = 0.011 apart in u, far above the rounding error of F.  The histogram is
+// therefore the one fill_profile builds (integer adds commute).
+//
+// Two parts: every lane first adds the first kLaneItems bins of its own
+// window, carrying each right edge over as the next bin's left edge (one CDF
+// per bin, no exchange); the bins beyond those, of the wider windows, are
+// then spread over the lanes, 31 per pass: a lane finds its track by a
+// shuffle search over the prefix sums of the remaining bins, evaluates the CDF
+// at its bin's left edge and takes the right edge from the next lane (items of
+// one track sit in consecutive lanes, lane 31 only supplies an edge).  With
+// kProfile = TEMPLATE the CDF value at edge i is the class template's Q[i] (tq:
+// the class's start in q), and the histogram is the one fill_template builds.
+constexpr int kLaneItems = 4;
+
+template <int kProfile>
+__device__ __forceinline__ int profile_q(int i, int j0, float zpoca, float inv_s, int tq,
+                                         const Consts& C) {
+  if constexpr (kProfile == PV_PROFILE_TEMPLATE) {
+    return PV_CHECK(tq + i < kTplCap, 1) ? __ldg(C.tpl->q + tq + i) : 0;
+  } else {
+    return quant_cdf(__fmul_rn(__fsub_rn(edge_of(j0 + i, C), zpoca), inv_s));
+  }
+}
+
 template <int kProfile = PV_PROFILE_CUBIC>
 __device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, float sigma,
                                                    int j0, int nb, int tq, const Consts& C) {
@@ -249,15 +269,30 @@ __device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, 
     if (s < kSMin) s = 0.0f;
     inv_s = (nb > 1 && s > 0.0f) ? __fdiv_rn(1.0f, s) : 0.0f;
   }
-  int incl = nb;                      // inclusive prefix of the window sizes
+  // part 1: the lane's own first bins
+  {
+    int ql = 0;
+#pragma unroll
+    for (int i = 0; i < kLaneItems; ++i) {
+      if (i < nb) {
+        const int qr = (i + 1 < nb) ? profile_q<kProfile>(i + 1, j0, zpoca, inv_s, tq, C) : kOne;
+        const int w = qr - ql;
+        const int j = j0 + i;
+        if (w > 0 && j >= 0 && j < C.nbins && PV_CHECK(j < C.ntiles * 32, 2))
+          atomicAdd(hist + j, static_cast<uint32_t>(w));
+        ql = qr;
+      }
+    }
+  }
+  // part 2: the remaining bins of the wider windows, spread over the lanes
+  const int nr = nb > kLaneItems ? nb - kLaneItems : 0;
+  int incl = nr;                      // inclusive prefix of the remaining sizes
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     int v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
   const int total = __shfl_sync(0xffffffffu, incl, 31);
-  // 31 items per pass: lane 31 only supplies the left edge of the item after
-  // lane 30's (the first item of the next pass)
   for (int base = 0; base < total; base += 31) {
     const int idx = base + lane;
     int L = 0;
@@ -267,16 +302,17 @@ __device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, 
     const int o_incl = __shfl_sync(0xffffffffu, incl, L);
     const int o_nb = __shfl_sync(0xffffffffu, nb, L);
     const int o_j0 = __shfl_sync(0xffffffffu, j0, L);
-    const int i = idx - (o_incl - o_nb);
+    // index in the window: the remaining bins start at kLaneItems
+    const int i = idx - (o_incl - (o_nb - kLaneItems)) + kLaneItems;
     const int j = o_j0 + i;
-    int ql = 0;                       // quantised CDF at the left edge of bin j
+    int ql = 0;                       // quantised CDF at the left edge of bin j (i > 0)
     if constexpr (kProfile == PV_PROFILE_TEMPLATE) {
       const int o_tq = __shfl_sync(0xffffffffu, tq, L);
-      if (idx < total && i > 0 && PV_CHECK(o_tq + i < kTplCap, 1)) ql = __ldg(C.tpl->q + o_tq + i);
+      if (idx < total && PV_CHECK(o_tq + i < kTplCap, 1)) ql = __ldg(C.tpl->q + o_tq + i);
     } else {
       const float o_z = __shfl_sync(0xffffffffu, zpoca, L);
       const float o_inv = __shfl_sync(0xffffffffu, inv_s, L);
-      if (idx < total && i > 0) ql = quant_cdf(__fmul_rn(__fsub_rn(edge_of(j, C), o_z), o_inv));
+      if (idx < total) ql = quant_cdf(__fmul_rn(__fsub_rn(edge_of(j, C), o_z), o_inv));
     }
     const int qn = __shfl_down_sync(0xffffffffu, ql, 1);
     const int qr = (i == o_nb - 1) ? kOne : qn;
@@ -522,14 +558,14 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     const uint64_t t_min = C.t_pp < C.t_gas ? C.t_pp : C.t_gas;
     const bool walk = lane < count && total >= t_min;
     int kept = 0, lo1 = 0, hi1 = 0, im1 = 0;
-    int lo2 = 0, hi2 = 0, im2 = 0;   // the recursive split also keeps the second piece
+    int lo2 = 0, hi2 = 0, im2 = 0;   // the first two kept pieces stay in registers
     if (walk) {
       split_pieces<kSplit>(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
         if (keep_piece(integral, im, C)) {
           if (kept == 0) {
             lo1 = lo; hi1 = hi; im1 = im;
-          } else if constexpr (kSplit == PV_SPLIT_RECURSIVE) {
-            if (kept == 1) { lo2 = lo; hi2 = hi; im2 = im; }
+          } else if (kept == 1) {
+            lo2 = lo; hi2 = hi; im2 = im;
           }
           ++kept;
         }
@@ -542,18 +578,12 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     }
     int n_kept = __shfl_sync(0xffffffffu, incl, 31);
     int pos = n_seeds + incl - kept;
-    bool rewalk = kept > 1 && pos < cap;
-    if (kept == 1 && pos < cap) {
+    // a proto-cluster with three or more kept pieces is walked again to write them
+    if (kept >= 1 && kept <= 2 && pos < cap) {
       put(pos, lo1, hi1, im1);
-    } else if constexpr (kSplit == PV_SPLIT_RECURSIVE) {
-      // the recursive split is the costlier walk: two pieces need none again
-      if (kept == 2 && pos < cap) {
-        put(pos, lo1, hi1, im1);
-        if (pos + 1 < cap) put(pos + 1, lo2, hi2, im2);
-        rewalk = false;
-      }
+      if (kept == 2 && pos + 1 < cap) put(pos + 1, lo2, hi2, im2);
     }
-    if (rewalk) {
+    if (kept > 2 && pos < cap) {
       split_pieces<kSplit>(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
         if (keep_piece(integral, im, C)) {
           if (pos < cap) put(pos, lo, hi, im);
@@ -578,13 +608,17 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     while (m) {
       int tb = __ffs(m) - 1;
       m &= m - 1;
-      int bin = (w * 32 + tb) * 32 + lane;
-      uint32_t v = (bin < C.nbins) ? N[bin] : 0u;
-      uint32_t vp = (bin >= 1 && bin - 1 < C.nbins) ? N[bin - 1] : 0u;
-      uint32_t vn = (bin + 1 < C.nbins) ? N[bin + 1] : 0u;
-      bool above = v > C.thr;
-      unsigned starts = __ballot_sync(0xffffffffu, above && !(vp > C.thr));
-      unsigned ends = __ballot_sync(0xffffffffu, above && !(vn > C.thr));
+      const int q = w * 32 + tb;
+      int bin = q * 32 + lane;
+      const uint32_t v = (bin < C.nbins) ? N[bin] : 0u;
+      const unsigned A = __ballot_sync(0xffffffffu, v > C.thr);
+      if (A == 0u) continue;
+      // the bins next to the tile: the last of tile q - 1, the first of q + 1
+      const int bp = q * 32 - 1, bn = q * 32 + 32;
+      const unsigned pa = (bp >= 0 && bp < C.nbins && N[bp] > C.thr) ? 1u : 0u;
+      const unsigned na = (bn < C.nbins && N[bn] > C.thr) ? 0x80000000u : 0u;
+      const unsigned starts = A & ~((A << 1) | pa);
+      const unsigned ends = A & ~((A >> 1) | na);
       if (starts & (1u << lane))
         pc_lo[(n_starts + __popc(starts & lt)) & (kRunRing - 1)] = static_cast<int16_t>(bin);
       if (ends & (1u << lane))

@@ -125,11 +125,11 @@ __device__ __forceinline__ void warp_slots(const int* cid, int n, int* base, int
   }
 }
 
-// The same placement, writing the vertex-ordered list of global track indices
-// (sorted[b0 + position] = b0 + t) instead of per-track slots; warp 0 only.
-template <typename CidT>
-__device__ __forceinline__ void warp_place(const CidT* cid, int n, int* base, int32_t* sorted,
-                                           int64_t b0) {
+// The same placement for the fused path: slot[t] = position of track t among
+// its event's tracks in vertex order (SlotT: int16 in shared memory for small
+// events, int32 in global scratch above that); warp 0 only.
+template <typename CidT, typename SlotT>
+__device__ __forceinline__ void warp_place(const CidT* cid, int n, int* base, SlotT* slot) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   for (int t0 = 0; t0 < n; t0 += 32) {
@@ -141,7 +141,7 @@ __device__ __forceinline__ void warp_place(const CidT* cid, int n, int* base, in
     int b = c >= 0 ? base[c] : 0;
     __syncwarp();
     if (c >= 0) {
-      if (PV_CHECK(b + rank < n, 6)) sorted[b0 + b + rank] = static_cast<int32_t>(b0 + t);
+      if (PV_CHECK(b + rank < n, 6)) slot[t] = static_cast<SlotT>(b + rank);
       if (lane == leader) base[c] = b + __popc(peers);
     }
     __syncwarp();
@@ -188,13 +188,7 @@ __device__ __forceinline__ void write_vertex(const Consts& C, const OutPtrs& O, 
 // against the find kernel's occupancy.
 __device__ __noinline__ void write_empty_vertex(const Consts& C, const OutPtrs& O,
                                                 const SeedOut* S, int e, int k) {
-  float xs = S->x[k], ys = S->y[k], zs = S->z[k];
-  if (S->bin[k] >= 0) {
-    zs = seed_z_from(S->nm[k], S->ni[k], S->np[k], S->bin[k], C);
-    xs = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
-    ys = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
-  }
-  write_vertex(C, O, e, k, xs, ys, zs, empty_fit(C));
+  write_vertex(C, O, e, k, S->x[k], S->y[k], S->z[k], empty_fit(C));
 }
 
 // Fit every vertex of one event (block-cooperative; used by the plain path).
@@ -330,6 +324,16 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
           r0 = T.x[i]; r1 = T.y[i]; r2 = T.z[i]; r3 = T.tx[i];
           r4 = T.ty[i]; r5 = T.cxx[i]; r6 = T.cxtx[i]; r7 = T.ctxtx[i];
         }
+        if constexpr ((MODE & kFit) != 0 && (MODE & kStage) == 0) {
+          // the fit-input pass reads the three y-covariance columns: bring
+          // this round's into L2 now
+          if (t < n) {
+            const int64_t i = b0 + t;
+            prefetch_l2(T.cyy + i);
+            prefetch_l2(T.cyty + i);
+            prefetch_l2(T.ctyty + i);
+          }
+        }
         Prep p;
         p.filled = false;
         p.zpoca = p.sigma = 0.0f;
@@ -341,13 +345,25 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
           if (PV_CHECK(!small || t < kSmallCap, 7))
             center[t] = static_cast<int16_t>(p.filled ? p.center : -1);
         }
-        if (p.filled) {
-          int q0 = (p.j0 < 0 ? 0 : p.j0) >> 5;
-          int q1 = (p.j1 >= C.nbins ? C.nbins - 1 : p.j1) >> 5;
-          for (int q = q0; q <= q1; ++q) {
-            uint32_t bit = 1u << (q & 31);
-            if (PV_CHECK((q >> 5) < kTileWords, 8) && !(tmask[q >> 5] & bit))
-              atomicOr(tmask + (q >> 5), bit);
+        {
+          // the 32-bin tiles the windows touch: each lane's range as four
+          // mask words, OR-reduced over the warp, one atomic per new word
+          int q0 = 1, q1 = 0;
+          if (p.filled) {
+            q0 = (p.j0 < 0 ? 0 : p.j0) >> 5;
+            q1 = (p.j1 >= C.nbins ? C.nbins - 1 : p.j1) >> 5;
+          }
+#pragma unroll
+          for (int w = 0; w < kTileWords; ++w) {
+            const int lo = q0 > 32 * w ? q0 : 32 * w;
+            const int hi = q1 < 32 * w + 31 ? q1 : 32 * w + 31;
+            uint32_t m = 0u;
+            if (lo <= hi) {
+              const int len = hi - lo + 1;
+              m = (len == 32 ? 0xffffffffu : ((1u << len) - 1u)) << (lo - 32 * w);
+            }
+            m = __reduce_or_sync(0xffffffffu, m);
+            if (lane == w && m != 0u && (tmask[w] & m) != m) atomicOr(tmask + w, m);
           }
         }
         warp_fill_profiles<PROFILE>(hist, p.zpoca, p.sigma, p.j0,
@@ -357,20 +373,36 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
       __syncthreads();
       // (c): seeds from the touched tiles (warp 0)
       if (warp == 0) {
-        // the seed position is computed here only when it is the output;
-        // otherwise the fit kernel derives it from the bins around the maximum
-        int K = warp_find_seeds<MODE == kFind, SPLIT>(hist, tmask, C, S, O.cap, pc_lo, pc_hi);
+        // (the seed positions are computed after the association, for the
+        // surviving seeds only)
+        int K = warp_find_seeds<false, SPLIT>(hist, tmask, C, S, O.cap, pc_lo, pc_hi);
         if (lane == 0) misc[2] = K;
       }
       __syncthreads();
       const int Kall = misc[2];
       const int K = Kall < O.cap ? Kall : O.cap;
-      // clear the touched tiles for the next event
-      for (int q = warp; q < C.ntiles; q += NW)
-        if ((tmask[q >> 5] >> (q & 31)) & 1u) hist[q * 32 + lane] = 0u;
+      // clear the touched tiles for the next event (warp w the tiles of mask
+      // word w, w + NW, ...)
+      for (int w = warp; w < kTileWords; w += NW) {
+        uint32_t m = tmask[w];
+        while (m) {
+          const int tb = __ffs(m) - 1;
+          m &= m - 1;
+          hist[(w * 32 + tb) * 32 + lane] = 0u;
+        }
+      }
       // (d1): association with the removal loop
       Ka = block_associate(center, cid, n, S, K, C, alive, part, cnt, misc + 3);
       if (tid < kTileWords) tmask[tid] = 0u;
+      // seed positions of the survivors: z from the bins around the maximum
+      // in binary64 (Sec. 3.3, R9), x and y on the beamline
+      if (tid < Ka) {
+        const float zs = seed_z_from(S->nm[tid], S->ni[tid], S->np[tid], S->bin[tid], C);
+        S->z[tid] = zs;
+        S->x[tid] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
+        S->y[tid] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
+      }
+      __syncthreads();
       for (int t = tid; t < n; t += NT) O.track_vertex[b0 + t] = cid[t];
       if (tid == 0) {
         O.n_per_event[e] = Ka;
@@ -416,12 +448,18 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
     }
 
     if (MODE & kFit) {
-      // tracks in vertex order and one work item per vertex with tracks; a
-      // vertex without tracks gets the (singular) result of an empty fit here
+      // each track's place in vertex order, one work item per vertex with
+      // tracks (a vertex without tracks gets the singular result of an empty
+      // fit here), then every track's fit inputs at its vertex's seed,
+      // written in vertex order for the fit kernel
       if (warp == 0) warp_offsets(cnt, Ka, voff, base);
       __syncthreads();
+      // after the association the center bins are spent: small events keep
+      // their slots in the same shared array
+      int16_t* s_slot = s_center;
       if (warp == 0) {
-        warp_place(cid, n, base, G.sorted, b0);
+        if (small) warp_place(cid, n, base, s_slot);
+        else warp_place(cid, n, base, G.slot + b0);
       } else if (warp == 1) {
         // one work item per vertex with tracks, in the list of its size class
         const unsigned lt = (1u << lane) - 1u;
@@ -459,21 +497,37 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
               w.off = static_cast<int>(b0 + voff[k]);
               w.e = e;
               w.kc = k | (cnt[k] << 8);
-              w.bin = S->bin[k];
-              if (w.bin >= 0) {
-                w.a = S->nm[k]; w.b = S->ni[k]; w.c = S->np[k];
-              } else {
-                w.a = __float_as_uint(S->x[k]);
-                w.b = __float_as_uint(S->y[k]);
-                w.c = __float_as_uint(S->z[k]);
-              }
-              w.pad = 0;
+              w.pad0 = 0;
+              w.x = __float_as_uint(S->x[k]);
+              w.y = __float_as_uint(S->y[k]);
+              w.z = __float_as_uint(S->z[k]);
+              w.pad1 = 0;
               if (PV_CHECK(idx >= 0, 9)) G.work[class_pick(G.cls_base, cl) + idx] = w;
             }
           } else {
             write_empty_vertex(C, O, S, e, k);
           }
         }
+      }
+      __syncthreads();
+      // fit inputs (the staged mode reads its first eight columns back from
+      // the device copy the fill wrote, the other three from host memory)
+      for (int t = tid; t < n; t += NT) {
+        const int c = static_cast<int>(cid[t]);
+        if (c < 0) continue;
+        const int sl = small ? static_cast<int>(s_slot[t]) : G.slot[b0 + t];
+        if (!PV_CHECK(sl >= 0 && sl < n && c < kMaxSeeds, 10)) continue;
+        const int64_t i = b0 + t;
+        float x, y, z, tx, ty, cxx, cxtx, ctxtx;
+        if constexpr ((MODE & kStage) != 0) {
+          x = G.stage[0][i]; y = G.stage[1][i]; z = G.stage[2][i]; tx = G.stage[3][i];
+          ty = G.stage[4][i]; cxx = G.stage[5][i]; cxtx = G.stage[6][i]; ctxtx = G.stage[7][i];
+        } else {
+          x = T.x[i]; y = T.y[i]; z = T.z[i]; tx = T.tx[i];
+          ty = T.ty[i]; cxx = T.cxx[i]; cxtx = T.cxtx[i]; ctxtx = T.ctxtx[i];
+        }
+        make_fit_track(x, y, z, tx, ty, cxx, cxtx, ctxtx, T.cyy[i], T.cyty[i], T.ctyty[i],
+                       S->x[c], S->y[c], S->z[c], G.A + b0 + sl, G.W + b0 + sl);
       }
     }
     __syncthreads();   // shared state is reused by the next event
@@ -482,14 +536,12 @@ find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
 
 // ---------------------------------------------------------------------------
 // vertex fit kernel (fused path, stage 2): every 8-lane group fits one vertex
-// of any event; warps take 4 work items at a time.
+// of any event from the fit inputs the find kernel wrote in vertex order;
+// warps take 4 work items at a time, largest size class first.
 
 template <int kAccum, int FT>
 __global__ void __launch_bounds__(FT)
 fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
-  // kLaneSlots fit inputs per thread: slot j of thread i at [j * FT + i]
-  __shared__ float4 sA[kLaneSlots * FT];
-  __shared__ float2 sW[kLaneSlots * FT];
   const int lane = threadIdx.x & 31;
   const int r = lane & (kGroup - 1);
   // the classes' listed vertices, largest class first
@@ -505,7 +557,7 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
     const int v = b + (lane >> 3);
     const bool has = v < n;
     VertexWork w;
-    w.off = 0; w.e = 0; w.kc = 0; w.bin = -1; w.a = w.b = w.c = 0u; w.pad = 0;
+    w.off = 0; w.e = 0; w.kc = 0; w.pad0 = 0; w.x = w.y = w.z = 0u; w.pad1 = 0;
     if (has) {
       long long q;
       if (v < n3) q = G.cls_base[3] + v;
@@ -516,59 +568,15 @@ fit_kernel(Consts C, TrackPtrs T, TrackScratch G, OutPtrs O) {
     }
     const int k = w.kc & 0xff;
     const int cntk = has ? (w.kc >> 8) : -1;
-    // seed position: given, or z_seed from the bins around the maximum
-    // (binary64, one lane per group) with x, y on the beamline
-    float zs = __uint_as_float(w.c);
-    if (has && w.bin >= 0 && r == 0) zs = seed_z_from(w.a, w.b, w.c, w.bin, C);
-    zs = __shfl_sync(0xffffffffu, zs, lane & ~(kGroup - 1));
-    float xs = __uint_as_float(w.a), ys = __uint_as_float(w.b);
-    if (w.bin >= 0) {
-      xs = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
-      ys = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
-    }
-    // this lane's tracks: fit inputs relative to the seed, read back by the
-    // same lane only, so they live in the lane's shared-memory slots (strided
-    // by the block size: conflict-free) unless the vertex is too large
-    float4* A;
-    float2* W;
-    int stride;
-    if (cntk <= kGroup * kLaneSlots) {
-      A = sA + threadIdx.x;
-      W = sW + threadIdx.x;
-      stride = FT;
-    } else {
-      A = G.A + w.off + r;
-      W = G.W + w.off + r;
-      stride = kGroup;
-    }
     // (a checked build that finds a bad vertex range fits no track for it;
     // the warp stays converged for the fit's shuffles)
     const int cnt_g = PV_CHECK(cntk <= 0 || (w.off >= 0 && w.off + cntk <= T.n_tracks), 11)
                           ? cntk : 0;
-    // two tracks per pass: both tracks' loads are in flight together
-    int s = r, q = 0;
-    for (; s + kGroup < cnt_g; s += 2 * kGroup, q += 2 * stride) {
-      const int t0 = G.sorted[w.off + s], t1 = G.sorted[w.off + s + kGroup];
-      if (!PV_CHECK(t0 >= 0 && t0 < T.n_tracks && t1 >= 0 && t1 < T.n_tracks, 12)) break;
-      const float a0 = T.x[t0], a1 = T.y[t0], a2 = T.z[t0], a3 = T.tx[t0], a4 = T.ty[t0];
-      const float a5 = T.cxx[t0], a6 = T.cxtx[t0], a7 = T.ctxtx[t0], a8 = T.cyy[t0];
-      const float a9 = T.cyty[t0], a10 = T.ctyty[t0];
-      const float b0 = T.x[t1], b1 = T.y[t1], b2 = T.z[t1], b3 = T.tx[t1], b4 = T.ty[t1];
-      const float b5 = T.cxx[t1], b6 = T.cxtx[t1], b7 = T.ctxtx[t1], b8 = T.cyy[t1];
-      const float b9 = T.cyty[t1], b10 = T.ctyty[t1];
-      make_fit_track(a0, a1, a2, a3, a4, a5, a6, a7, a8, a9, a10, xs, ys, zs, A + q, W + q);
-      make_fit_track(b0, b1, b2, b3, b4, b5, b6, b7, b8, b9, b10, xs, ys, zs, A + q + stride,
-                     W + q + stride);
-    }
-    if (s < cnt_g) {
-      const int t = G.sorted[w.off + s];
-      if (PV_CHECK(t >= 0 && t < T.n_tracks, 12))
-        make_fit_track(T.x[t], T.y[t], T.z[t], T.tx[t], T.ty[t], T.cxx[t], T.cxtx[t],
-                       T.ctxtx[t], T.cyy[t], T.cyty[t], T.ctyty[t], xs, ys, zs, A + q, W + q);
-    }
     VertexOut out;
-    group_fit<kAccum>(A, W, stride, cnt_g, C, &out);
-    if (has && r == 0) write_vertex(C, O, w.e, k, xs, ys, zs, out);
+    group_fit<kAccum>(G.A + w.off + r, G.W + w.off + r, kGroup, cnt_g, C, &out);
+    if (has && r == 0)
+      write_vertex(C, O, w.e, k, __uint_as_float(w.x), __uint_as_float(w.y), __uint_as_float(w.z),
+                   out);
   }
 }
 
@@ -1087,32 +1095,23 @@ static void launch_find(int nt, int grid, size_t sm, cudaStream_t st, const Cons
 
 cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
                          const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
-                         cudaStream_t st, int* n_launches, cudaEvent_t fit_after) {
+                         cudaStream_t st, int* n_launches) {
   size_t sm = fused_smem_bytes(C.nbins, mode);
   cudaError_t err = cudaMemsetAsync(ws.counters, 0, kCounterInts * sizeof(int), st);
   if (err != cudaSuccess) return err;
   if (mode == kFindFitStaged) {
-    // GPU flavour only; the fit gathers from the device copy
+    // GPU flavour only
     if (L.find_nt == 96)
       find_kernel<kFindFitStaged, 96><<<L.find_grid, 96, sm, st>>>(C, T, S, O, ws);
     else
       find_kernel<kFindFitStaged, 128><<<L.find_grid, 128, sm, st>>>(C, T, S, O, ws);
-    if (fit_after) {
-      err = cudaStreamWaitEvent(st, fit_after, 0);
-      if (err != cudaSuccess) return err;
-    }
-    TrackPtrs D = T;
-    D.x = ws.stage[0]; D.y = ws.stage[1]; D.z = ws.stage[2]; D.tx = ws.stage[3];
-    D.ty = ws.stage[4]; D.cxx = ws.stage[5]; D.cxtx = ws.stage[6]; D.ctxtx = ws.stage[7];
-    D.cyy = ws.stage[8]; D.cyty = ws.stage[9]; D.ctyty = ws.stage[10];
-    if (L.fit_nt == 128) launch_fit_ft<128>(C.accum_mode, L.fit_grid, st, C, D, ws, O);
-    else launch_fit_ft<256>(C.accum_mode, L.fit_grid, st, C, D, ws, O);
-    *n_launches += 2;
-    return cudaGetLastError();
+  } else if (mode == kFind) {
+    launch_find<kFind>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
+  } else if (mode == kFit) {
+    launch_find<kFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
+  } else {
+    launch_find<kFindFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
   }
-  if (mode == kFind) launch_find<kFind>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
-  else if (mode == kFit) launch_find<kFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
-  else launch_find<kFindFit>(L.find_nt, L.find_grid, sm, st, C, T, S, O, ws);
   ++*n_launches;
   if (mode & kFit) {
     if (L.fit_nt == 128) launch_fit_ft<128>(C.accum_mode, L.fit_grid, st, C, T, ws, O);

@@ -32,17 +32,17 @@ struct SeedPtrs {            // seeds read by the fit-only kernel
   int32_t cap;
 };
 
-// One vertex to fit: its tracks are sorted[off .. off + cnt) (global track
-// indices in track-index order) and its results go to row e, column k of the
-// outputs.  bin >= 0: the seed comes from the histogram, a, b, c = N[bin-1],
-// N[bin], N[bin+1]; bin < 0: a, b, c are the bit patterns of the seed's x, y, z.
+// One vertex to fit: its fit inputs are A[off .. off + cnt), W[off .. off +
+// cnt) (its tracks in track-index order, written by the find kernel) and its
+// results go to row e, column k of the outputs; x, y, z are the bit patterns
+// of the seed position the inputs are relative to.
 struct VertexWork {
   int off;
   int e;
   int kc;           // k | cnt << 8
-  int bin;
-  uint32_t a, b, c;
-  int pad;
+  int pad0;
+  uint32_t x, y, z;
+  int pad1;
 };
 
 // The vertex work list is split by size class (tracks per vertex: 1-8,
@@ -59,22 +59,18 @@ constexpr int kClassMinTracks[kWorkClasses] = {1, 9, 17, 33};
 struct TrackScratch {
   int16_t* center;      // per track, events above kSmallCap tracks: center bin
   int8_t* cid;          // and vertex index
-  int32_t* sorted;      // per track: global track indices in vertex order
-  float4* A;            // per track: fit inputs in vertex order
-  float2* W;
+  int32_t* slot;        // per track, events above kSmallCap tracks: position of
+                        // the track's fit inputs in its event's vertex order
+  float4* A;            // per track: fit inputs in vertex order (X, Y, tx, ty)
+  float2* W;            //   and their weights (1/V_xx, 1/V_yy) at the seed z
   VertexWork* work;     // vertex work lists, one region per size class
   long long cls_base[kWorkClasses];   // first entry of each class's region
   int cls_cap[kWorkClasses];    // its capacity
   int* counters;        // [0] next event, [1 + c] vertices listed in class c,
                         // [1 + kWorkClasses] next vertex to fit
-  float* stage[11];     // kStage: device copy of the 11 track columns (TrackPtrs order)
+  float* stage[8];      // kStage: device copy of the first 8 track columns (TrackPtrs order)
 };
 constexpr int kCounterInts = 8;
-
-// fit inputs each fit-kernel thread keeps in shared memory: vertices of up to
-// 8 x kLaneSlots tracks are fitted from shared memory, larger ones from the
-// global scratch (24 bytes per slot: 24 KB per 128-thread block)
-constexpr int kLaneSlots = 8;
 
 // a[c] with constant indices only (a kernel parameter indexed at run time
 // would be copied to local memory)
@@ -85,9 +81,9 @@ __host__ __device__ __forceinline__ V class_pick(const V (&a)[kWorkClasses], int
 
 enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3, kStage = 4 };
 // kFindFit | kStage: the tracks are in host memory the device can address; the
-// find kernel reads its eight columns there once and writes them to a device
-// copy (TrackScratch::stage) that the fit kernel gathers from; the other three
-// columns are copied in beside it
+// find kernel reads every column there once: the eight its steps (a)-(b) need
+// in the fill, writing them to a device copy (TrackScratch::stage) that its
+// fit-input pass reads back, and the other three in that pass
 constexpr int kFindFitStaged = kFindFit | kStage;
 
 constexpr int kSmallCap = 256;      // tracks kept in shared memory per event
@@ -143,12 +139,10 @@ struct LaunchCfg {
 };
 
 // Enqueues the fused path: counter reset, find kernel, then (modes with a fit)
-// the vertex fit kernel.  *n_launches receives the kernels enqueued.  In the
-// staged mode the fit kernel also waits for fit_after (if given): the copy of
-// the three columns the find kernel does not read.
+// the vertex fit kernel.  *n_launches receives the kernels enqueued.
 cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, const SeedPtrs& S,
                          const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
-                         cudaStream_t st, int* n_launches, cudaEvent_t fit_after = nullptr);
+                         cudaStream_t st, int* n_launches);
 
 // The checked build's record of out-of-bounds indices (count, first code),
 // reset by the call; false in the default build, which has no checks.

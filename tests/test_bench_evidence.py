@@ -1,7 +1,8 @@
 """The benchmark's link to its ncu evidence (CPU): the DRAM traffic of the
-committed capture is reported only while the kernel sources are the ones it
-was taken on.  Host-side library code does not enter the hash; kernel code
-and the header's constants do."""
+committed capture is reported only while the library's CUDA sources (kernels
+and the host code that lays out their scratch and sizes their grids), the
+header's constants and the nvcc flags are the ones it was taken on.  Header
+comments do not enter the hash."""
 import os
 import shutil
 import sys
@@ -36,8 +37,7 @@ def test_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     h0 = bench._sources_hash()
     traffic = bench._profiled_traffic(10_000)
     assert traffic is not None and traffic > 0
-    # host-side library code and header comments do not invalidate it
-    _append(os.path.join(root, "paper_2412_14966_gb300", "csrc", "pv_api.cu"), "\n// host\n")
+    # header comments do not invalidate it
     _append(os.path.join(root, "include", "pv.h"), "\n/* a comment */\n")
     assert bench._sources_hash() == h0
     assert bench._profiled_traffic(10_000) == traffic
@@ -47,11 +47,20 @@ def test_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     assert h1 != h0 and bench._profiled_traffic(10_000) is None
 
 
+def test_traffic_is_dropped_when_the_build_flags_change(tmp_path, monkeypatch):
+    _copy_tree(tmp_path, monkeypatch)
+    from paper_2412_14966_gb300 import build
+    h0 = bench._sources_hash()
+    monkeypatch.setattr(build, "NVCC_FLAGS", build.NVCC_FLAGS + ["-DSOMETHING"])
+    assert bench._sources_hash() != h0
+    assert bench._profiled_traffic(10_000) is None
+
+
 def test_traffic_is_dropped_when_a_kernel_changes(tmp_path, monkeypatch):
     root = _copy_tree(tmp_path, monkeypatch)
     h0 = bench._sources_hash()
     assert bench._profiled_traffic(10_000) is not None
-    for f in ("pv_device.cuh", "pv_kernels.cu", "pv_kernels.cuh"):
+    for f in ("pv_device.cuh", "pv_kernels.cu", "pv_kernels.cuh", "pv_api.cu"):
         p = os.path.join(root, "paper_2412_14966_gb300", "csrc", f)
         saved = open(p).read()
         _append(p, "\n// changed\n")
