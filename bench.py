@@ -272,6 +272,62 @@ def cpu_baseline(batch, max_seconds: float = 15.0) -> dict:
             "single_thread": one}
 
 
+def _ac_errors(batch, p) -> dict:
+    """Binary32 error of steps (a)-(c) of one batch against the oracle's
+    binary64 replay (the GPU path reproduces the binary32 sequence bit for
+    bit): z_poca (um) and relative sigma_poca over the filled tracks, the
+    profile's per-bin error against the Gaussian bin integral (track units),
+    and the seed z (um) where both find the same seeds."""
+    import oracle
+    pr32 = oracle.prepare_f32(batch.tracks, p)
+    pr64 = oracle.prepare_f64(batch.tracks, p)
+    f = pr32["filled"] > 0
+    dz = np.abs(pr32["zpoca"].astype(np.float64) - pr64["zpoca"])[f] * 1e3
+    ds = (np.abs(pr32["sigma"].astype(np.float64) - pr64["sigma"]) / pr64["sigma"])[f]
+    prof = oracle.profile_error(batch.tracks, p)
+    f32 = oracle.find_batch(batch, p)
+    f64 = oracle.find_batch_f64(batch, p)
+    same = f32["n"] == f64["n"]
+    K = f32["bin"].shape[1]
+    live = np.arange(K)[None, :] < f32["n"][:, None]
+    m = same[:, None] & live & (f32["bin"] == f64["bin"])
+    dzs = np.abs(f32["z"].astype(np.float64) - f64["z"])[m] * 1e3
+    rms = lambda a: float(np.sqrt(np.mean(a ** 2))) if a.size else 0.0
+    return {"events": batch.n_events, "tracks_filled": int(f.sum()),
+            "zpoca_um": {"max": float(dz.max()), "rms": rms(dz)},
+            "sigma_rel": {"max": float(ds.max()), "rms": rms(ds)},
+            "profile_bin_err": {"max": prof["max"], "rms": prof["rms"], "bins": prof["bins"]},
+            "seed_z_um": {"max": float(dzs.max()) if dzs.size else 0.0, "rms": rms(dzs),
+                          "seeds": int(m.sum()), "events_same_seeds": float(same.mean())}}
+
+
+def oracle_reports(batch, gpu: dict) -> dict:
+    """The CPU-baseline leg's error reports, the oracle being the reference:
+    the binary32 error of steps (a)-(c) on the nominal batch and on 1,000
+    high pile-up events, and the GPU's fitted vertices of the timed batch
+    against the oracle's binary64 fit (max and RMS in um over the vertices
+    whose iteration counts agree)."""
+    import oracle
+    from paper_2412_14966_gb300 import synthetic
+    p = oracle.default_params()
+    out = {"nominal": _ac_errors(batch, p),
+           "pileup_1000": _ac_errors(synthetic.workload_pileup(n_events=1000), p)}
+    ref = oracle.find_batch(batch, p)
+    fit = oracle.fit_batch(batch, ref, p)
+    E, K = fit["z"].shape
+    live = np.arange(K)[None, :] < ref["n"][:, None]
+    ok = live & ((fit["status"] & oracle.SINGULAR) == 0) & (gpu["n_iter"][:E, :K] == fit["n_iter"])
+    f64 = lambda a: np.asarray(a, np.float64)
+    dxy = np.concatenate([np.abs(f64(gpu[k][:E, :K]) - f64(fit[k]))[ok] for k in ("x", "y")]) * 1e3
+    dz = np.abs(f64(gpu["z"][:E, :K]) - f64(fit["z"]))[ok] * 1e3
+    out["fit_um"] = {"vertices": int(ok.sum()), "xy_max": float(dxy.max()),
+                     "xy_rms": float(np.sqrt(np.mean(dxy ** 2))), "z_max": float(dz.max()),
+                     "z_rms": float(np.sqrt(np.mean(dz ** 2))),
+                     "iteration_counts_differ": int((live & ~ok).sum() -
+                                                    ((fit["status"] & oracle.SINGULAR) != 0)[live].sum())}
+    return out
+
+
 def serving_run(pv, ctx, offered_hz: float, duration_s: float = 1.0, tick_s: float = 100e-6,
                 seed: int = 7, mix=None) -> dict:
     """Open-loop serving: events of the uneven mixture workload (mu ~ U(1, 12),
@@ -630,6 +686,7 @@ def run_ours(args):
         line["serving_sweep"] = sweep
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch)
+        line["binary32_error"] = oracle_reports(batch, vo)
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -149,6 +149,8 @@ def lib():
         L.oc_seeds_from_hist.restype = C.c_int
         L.oc_associate_bins.argtypes = [ip, C.c_int64, ip, ip, ip, C.c_int, pp, ip, ip]
         L.oc_associate_bins.restype = C.c_int
+        L.oc_find_batch_f64.argtypes = [arr11, i64p, C.c_int32, pp, dp, ip, ip]
+        L.oc_profile_error.argtypes = [arr11, C.c_int64, pp, dp]
         L.oc_mv_fit_batch.argtypes = [arr11, i64p, C.c_int32, pp, P(MvParams), fp, fp, fp, ip,
                                       dp, dp, dp, dp, dp, dp, ip, ip, ip, ip]
         _LIB = L
@@ -195,6 +197,37 @@ def prepare_f64(tracks: dict, p: Params) -> dict:
     sg = np.zeros(n, np.float64)
     lib().oc_prepare_tracks_f64(arr, n, C.byref(p), _ptr(zp, C.c_double), _ptr(sg, C.c_double))
     return {"zpoca": zp, "sigma": sg}
+
+
+def find_batch_f64(batch, p: Params) -> dict:
+    """Steps (a)-(d1) replayed in binary64 (z_poca, sigma_poca, window and
+    cubic CDF in binary64, the same integer histogram rules, peak search and
+    association): every event's surviving seeds, their maximum bin and their z
+    before any rounding to binary32.  For error reports only."""
+    arr, keep = _tracks_arg(batch.tracks)
+    E = batch.n_events
+    cap = p.max_seeds
+    z = np.zeros((E, cap), np.float64)
+    b = np.zeros((E, cap), np.int32)
+    n = np.zeros(E, np.int32)
+    offs = np.ascontiguousarray(batch.offsets, np.int64)
+    lib().oc_find_batch_f64(arr, _ptr(offs, C.c_int64), E, C.byref(p), _ptr(z, C.c_double),
+                            _ptr(b, C.c_int32), _ptr(n, C.c_int32))
+    return {"z": z, "bin": b, "n": n}
+
+
+def profile_error(tracks: dict, p: Params) -> dict:
+    """Per-bin error of the binary32 integer profile (reading R3, or R17 for
+    profile_mode 1) against the Gaussian bin integral of the binary64 z_poca
+    and sigma_poca, over the bins within 5 sigma of every filled track, in
+    track units: largest and RMS, and the largest truncation of a window (its
+    weight sum against the Gaussian mass in range).  For error reports only."""
+    arr, keep = _tracks_arg(tracks)
+    n = len(keep[0])
+    out = np.zeros(4, np.float64)
+    lib().oc_profile_error(arr, n, C.byref(p), _ptr(out, C.c_double))
+    return {"max": float(out[0]), "rms": float(np.sqrt(out[1] / max(out[2], 1.0))),
+            "bins": int(out[2]), "truncation_max": float(out[3])}
 
 
 def track_profile(zpoca: float, sigma: float, p: Params):

@@ -445,9 +445,30 @@ static float oc_seed_z(const uint32_t* N, int nbins, int i, const oc_params* p) 
   return (float)z;
 }
 
+/* z_seed of R9 before its rounding to binary32 (error reports only) */
+static double oc_seed_z64(const uint32_t* N, int nbins, int i, const oc_params* p) {
+  int64_t nm = (i > 0) ? (int64_t)N[i - 1] : 0;
+  int64_t np = (i + 1 < nbins) ? (int64_t)N[i + 1] : 0;
+  int64_t ni = (int64_t)N[i];
+  int64_t num = np - nm;
+  int64_t den = 2 * ni - np - nm;
+  double delta = den > 0 ? 0.5 * ((double)num / (double)den) : 0.0;
+  return (double)p->z_min + ((double)i + 0.5) * (double)p->dz + delta * (double)p->dz;
+}
+
+static int oc_clusters_core(const uint32_t* N, const oc_params* p, oc_seed* seeds, int cap,
+                            double* z64);
+
 /* All seeds of one event histogram, z-ordered.  Returns the number of seeds
  * (which may exceed cap; only cap are stored). */
 int oc_clusters_from_hist(const uint32_t* N, const oc_params* p, oc_seed* seeds, int cap) {
+  return oc_clusters_core(N, p, seeds, cap, NULL);
+}
+
+/* The same, also giving each stored seed's z before the binary32 rounding
+ * in z64 (when not NULL). */
+static int oc_clusters_core(const uint32_t* N, const oc_params* p, oc_seed* seeds, int cap,
+                            double* z64) {
   int nbins = oc_nbins(p);
   int gas_bin = oc_bin_f32(p->z_gas, p, nbins);
   int n = 0;
@@ -471,6 +492,7 @@ int oc_clusters_from_hist(const uint32_t* N, const oc_params* p, oc_seed* seeds,
         seeds[n].bin = im;
         float zs = oc_seed_z(N, nbins, im, p);
         seeds[n].z = zs;
+        if (z64) z64[n] = oc_seed_z64(N, nbins, im, p);
         seeds[n].x = p->x_b + p->tx_b * zs;
         seeds[n].y = p->y_b + p->ty_b * zs;
       }
@@ -1125,4 +1147,134 @@ int oc_mv_fit_batch(const float* const* T, const int64_t* offsets, int32_t n_eve
     free(E); free(ft); free(comp); free(prev);
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* binary64 replay of steps (a)-(d1), for error reports only                 */
+
+/* The cubic profile of R3 evaluated in binary64 from the binary64 z_poca and
+ * sigma_poca, quantised with the same rule: every quantity of step (a) and
+ * (b) in binary64, the histogram and everything after it integer as before. */
+static void oc_event_histogram_f64(const float* const* T, int64_t begin, int64_t end,
+                                   const oc_params* p, uint32_t* hist, int32_t* center) {
+  int nbins = oc_nbins(p);
+  memset(hist, 0, sizeof(uint32_t) * (size_t)nbins);
+  const double zmin = p->z_min, dz = p->dz;
+  for (int64_t t = begin; t < end; ++t) {
+    double zp, sig;
+    oc_prepare_f64(T[0][t], T[1][t], T[2][t], T[3][t], T[4][t], T[5][t], T[6][t], T[7][t],
+                   p, &zp, &sig);
+    center[t - begin] = -1;
+    double dtx = (double)T[3][t] - (double)p->tx_b, dty = (double)T[4][t] - (double)p->ty_b;
+    if (!(dtx * dtx + dty * dty > 0.0) || !isfinite(zp) || !isfinite(sig)) continue;
+    double qc = floor((zp - zmin) / dz);
+    if (!(qc >= 0.0) || qc >= (double)nbins) continue;
+    double smax = zp < (double)p->z_gas ? (double)p->sigma_max_gas : (double)p->sigma_max_pp;
+    if (!(sig <= smax)) continue;
+    center[t - begin] = (int32_t)qc;
+    double sp = 2.23606797749979 * sig;
+    if (sp < (double)OC_S_MIN) sp = 0.0;
+    int j0 = (int)floor((zp - sp - zmin) / dz), j1 = (int)floor((zp + sp - zmin) / dz);
+    int32_t qprev = 0;
+    for (int j = j0; j <= j1; ++j) {
+      int32_t qnext = OC_ONE;
+      if (j < j1) {
+        double u = (zmin + (double)(j + 1) * dz - zp) / sp;
+        double F = u <= -1.0 ? 0.0 : (u >= 1.0 ? 1.0 : 0.5 + u * (0.75 - 0.25 * u * u));
+        long q = lrint(F * OC_ONE);
+        qnext = (int32_t)(q < 0 ? 0 : (q > OC_ONE ? OC_ONE : q));
+      }
+      if (qnext < qprev) qnext = qprev;
+      if (j >= 0 && j < nbins) hist[j] += (uint32_t)(qnext - qprev);
+      qprev = qnext;
+    }
+  }
+}
+
+/* Surviving seeds of every event (cap per event, row-major): their maximum bin
+ * and z in binary64. */
+int oc_find_batch_f64(const float* const* T, const int64_t* offsets, int32_t n_events,
+                      const oc_params* p, double* seed_z, int32_t* seed_bin, int32_t* n_seeds) {
+  int nbins = oc_nbins(p);
+  int cap = p->max_seeds;
+  uint32_t* hist = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nbins);
+  oc_seed* seeds = (oc_seed*)malloc(sizeof(oc_seed) * (size_t)(cap > 0 ? cap : 1));
+  double* z64 = (double*)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+  int32_t* keep = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+  for (int32_t e = 0; e < n_events; ++e) {
+    int64_t b = offsets[e], en = offsets[e + 1];
+    int64_t n = en - b;
+    int32_t* center = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t* cl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    oc_event_histogram_f64(T, b, en, p, hist, center);
+    int K = oc_clusters_core(hist, p, seeds, cap, z64);
+    if (K > cap) K = cap;
+    int Ka = oc_associate(center, n, seeds, K, p, keep, cl);
+    int q = 0;
+    for (int k = 0; k < K; ++k) {
+      if (!keep[k]) continue;
+      seed_z[(size_t)e * cap + q] = z64[k];
+      seed_bin[(size_t)e * cap + q] = seeds[k].bin;
+      q++;
+    }
+    n_seeds[e] = Ka;
+    free(center);
+    free(cl);
+  }
+  free(hist);
+  free(seeds);
+  free(z64);
+  free(keep);
+  return 0;
+}
+
+/* Per-bin error of the binary32 profile (R3 cubic, or R17 templates) against
+ * the Gaussian bin integral of the binary64 z_poca and sigma_poca, over the
+ * bins within 5 sigma of z_poca of every filled track: out[0] = largest
+ * |w / ONE - G|, out[1] = sum of squares, out[2] = number of bins, out[3] =
+ * largest |sum of the window's weights / ONE - Gaussian mass inside the
+ * histogram| (the window's truncation). */
+void oc_profile_error(const float* const* T, int64_t n, const oc_params* p, double* out) {
+  int nbins = oc_nbins(p);
+  oc_tpl store;
+  const oc_tpl* tpl = oc_tpl_for(p, &store);
+  int cap = nbins + 2 * OC_TPL_MAX_HALF + 8;
+  uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)cap);
+  double emax = 0.0, ss = 0.0, cnt = 0.0, tmax = 0.0;
+  for (int64_t t = 0; t < n; ++t) {
+    oc_prep32 r;
+    oc_prepare_f32(T[0][t], T[1][t], T[2][t], T[3][t], T[4][t], T[5][t], T[6][t], T[7][t],
+                   p, tpl, nbins, &r);
+    if (!r.filled) continue;
+    double zp, sig;
+    oc_prepare_f64(T[0][t], T[1][t], T[2][t], T[3][t], T[4][t], T[5][t], T[6][t], T[7][t],
+                   p, &zp, &sig);
+    if (!(sig > 0.0)) continue;
+    int k = oc_profile_weights(&r, p, tpl, w, cap);
+    int g0 = (int)floor((zp - 5.0 * sig - p->z_min) / p->dz);
+    int g1 = (int)floor((zp + 5.0 * sig - p->z_min) / p->dz);
+    int lo = g0 < r.j0 ? g0 : r.j0, hi = g1 > r.j1 ? g1 : r.j1;
+    if (lo < 0) lo = 0;
+    if (hi > nbins - 1) hi = nbins - 1;
+    double wsum = 0.0, gsum = 0.0;
+    for (int j = lo; j <= hi; ++j) {
+      double wj = (j >= r.j0 && j <= r.j1 && j - r.j0 < k) ? (double)w[j - r.j0] / OC_ONE : 0.0;
+      double e0 = (double)p->z_min + (double)j * p->dz, e1 = e0 + p->dz;
+      double g = oc_phi((e1 - zp) / sig) - oc_phi((e0 - zp) / sig);
+      double d = fabs(wj - g);
+      if (d > emax) emax = d;
+      ss += d * d;
+      cnt += 1.0;
+      wsum += wj;
+      gsum += g;
+    }
+    double tr = fabs(wsum - gsum);
+    if (tr > tmax) tmax = tr;
+  }
+  free(w);
+  oc_tpl_free(&store);
+  out[0] = emax;
+  out[1] = ss;
+  out[2] = cnt;
+  out[3] = tmax;
 }
