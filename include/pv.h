@@ -236,23 +236,47 @@ int pv_check_report(uint32_t* count, uint32_t* first_code);
  * copied back whole.  Blocking. */
 int pv_run_host(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, void* cuda_stream);
 
-/* Serving.  pv_submit admits a request (device tracks and outputs, borrowed
- * until pv_poll reports done) if the serving pool has room for it, and
- * schedules it with other admitted requests; it never blocks.  *ticket
- * identifies the request.  PV_ERR_BUSY if the queue is full,
- * PV_ERR_NOMEM if the request alone exceeds pool_bytes. */
+/* Serving: continuous batching on the device.  pv_submit queues a request
+ * (device tracks and outputs, borrowed until pv_poll reports done) and never
+ * blocks.  A request is admitted when the serving pool (pool_bytes of device
+ * memory; 31 bytes per track of scratch) has room for it -- any waiting
+ * request that fits, not only the oldest -- and then written into a request
+ * ring in pinned host memory that a persistent serving kernel reads: its
+ * CTAs claim the published events of all admitted requests one at a time, run
+ * steps (a)-(d3) on each (the fused path's find and fit, the event's vertices
+ * fitted in the same CTA) and stamp a request's completion with the GPU's
+ * global timer when its last event finishes.  Requests that arrive while
+ * others run overlap with them on the device; a request's results equal those
+ * of pv_fit_batch with seeds == NULL on the same context.  *ticket identifies
+ * the request.  PV_ERR_BUSY if 4,096 requests already wait for admission,
+ * PV_ERR_NOMEM if the request alone exceeds the pool.  The serving kernel
+ * occupies the device while it runs; it ends after 2 ms (or max_spin_ns, if
+ * shorter) without an event to claim, and pv_submit / pv_poll start it again
+ * while requests are in flight. */
 int pv_submit(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, uint64_t* ticket);
 
 /* Non-blocking completion check: *done = 1 once the request's outputs are
- * complete in device memory (and its latency recorded), else 0.
- * PV_ERR_NOTFOUND for an unknown or already retired ticket. */
+ * complete in device memory, else 0; also admits waiting requests and keeps
+ * the serving kernel running.  PV_ERR_NOTFOUND for an unknown or already
+ * retired ticket. */
 int pv_poll(pv_ctx* ctx, uint64_t ticket, int* done);
 
-/* Latency of a completed request in nanoseconds, from pv_submit to the moment
- * the stream reached the end of its work, then retires the ticket (later
- * calls with it return PV_ERR_NOTFOUND).  PV_ERR_NOTFOUND if the ticket is
- * unknown or not yet done. */
+/* Latency of a completed request in nanoseconds, from pv_submit to the
+ * device's completion stamp of its last event (the GPU's global timer,
+ * calibrated against the host clock when the serving pool is set up), then
+ * retires the ticket (later calls with it return PV_ERR_NOTFOUND).
+ * PV_ERR_NOTFOUND if the ticket is unknown or not yet done. */
 int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns);
+
+/* Sets up the serving pool and starts the serving kernel now, with or without
+ * requests (it ends on its own after its idle bound, see pv_submit). */
+int pv_serve_start(pv_ctx* ctx);
+
+/* *running = 1 while the serving kernel runs; *last_exit = how its last run
+ * ended when it is not running: PV_OK (stopped by pv_destroy),
+ * PV_ERR_TIMEOUT (no event to claim within its idle bound), -1 if it never
+ * ended.  Either pointer may be NULL. */
+int pv_serve_status(pv_ctx* ctx, int* running, int* last_exit);
 
 /* Steps (a)-(d3) as one fused pass, like pv_fit_batch with seeds == NULL,
  * but without allocating device memory.  The paper has no counterpart: this

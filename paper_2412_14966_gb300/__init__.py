@@ -36,7 +36,7 @@ EXPORTED = (
     "pv_extrapolate_batch", "pv_histogram_batch", "pv_num_bins", "pv_run_host", "pv_submit",
     "pv_poll", "pv_request_latency_ns", "pv_strerror", "pv_last_cuda_error", "pv_launch_count",
     "pv_find_fit_static", "pv_autotune", "pv_launch_config", "pv_set_launch_config",
-    "pv_fit_multi", "pv_check_report", "pv_device_bytes",
+    "pv_fit_multi", "pv_check_report", "pv_device_bytes", "pv_serve_start", "pv_serve_status",
 )
 
 
@@ -131,6 +131,8 @@ def load():
     L.pv_launch_count.restype = C.c_uint64
     L.pv_device_bytes.argtypes = [C.c_void_p]
     L.pv_device_bytes.restype = C.c_uint64
+    L.pv_serve_start.argtypes = [C.c_void_p]
+    L.pv_serve_status.argtypes = [C.c_void_p, P(C.c_int), P(C.c_int)]
     L.pv_find_fit_static.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
     L.pv_autotune.argtypes = [C.c_void_p, P(pv_tracks), P(pv_vertices), C.c_void_p]
     L.pv_set_launch_config.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
@@ -413,6 +415,16 @@ class Context:
         done = C.c_int()
         self._check(self.lib.pv_poll(self.h, C.c_uint64(ticket), C.byref(done)), "pv_poll")
         return bool(done.value)
+
+    def serve_start(self):
+        """``pv_serve_start``: start the serving kernel now."""
+        self._check(self.lib.pv_serve_start(self.h), "pv_serve_start")
+
+    def serve_status(self) -> tuple:
+        """``pv_serve_status``: (running, last exit code)."""
+        r, x = C.c_int(0), C.c_int(0)
+        self._check(self.lib.pv_serve_status(self.h, C.byref(r), C.byref(x)), "pv_serve_status")
+        return bool(r.value), int(x.value)
 
     def latency_ns(self, ticket: int) -> int:
         ns = C.c_uint64()

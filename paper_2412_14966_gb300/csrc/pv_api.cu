@@ -148,13 +148,15 @@ struct PlainLayout {
 
 // ---- serving --------------------------------------------------------------
 
-constexpr int kServeStreams = 8;   // measured: 8 serve 28.8 M events/s at 30 M offered, 4 serve 27.0 M, 16 no more
 // pv_run_host: event chunks in flight (measured on the nominal batch: 2
-// chunks 0.64 ms per step, 3 0.65, 4 0.69, 8 0.81 — every chunk pays its
+// chunks 0.64 ms per step, 3 0.65, 4 0.69, 8 0.81 -- every chunk pays its
 // copies' set-up and the kernels' tail, and the host link is the bound)
 constexpr int kRunHostChunks = 2;
 constexpr int64_t kRunHostChunkEvents = 2048;  // fewest events per chunk
-constexpr size_t kMaxQueued = 4096;
+constexpr size_t kMaxQueued = 4096;            // requests waiting for admission
+// the serving kernel ends after this long without an event to claim (or
+// max_spin_ns if shorter); the next submit or poll starts it again
+constexpr uint64_t kServeIdleNs = 2000000;
 
 struct Request {
   uint64_t ticket = 0;
@@ -162,11 +164,10 @@ struct Request {
   pv_vertices out{};
   size_t bytes = 0;
   size_t arena_off = 0;
-  uint64_t t_submit = 0;
-  std::atomic<uint64_t> t_done{0};
-  std::atomic<int> done{0};
-  bool admitted = false;
-  int stream = 0;
+  uint64_t t_submit = 0;   // host steady clock
+  uint64_t t_done = 0;     // host steady clock (from the device's completion stamp)
+  uint64_t seq = 0;        // admission number (0: not admitted)
+  bool done = false;
 };
 
 // First-fit allocator over [0, size) with out-of-order frees.
@@ -244,17 +245,28 @@ struct pv_ctx {
   size_t rh_off_cap = 0;
   std::atomic<uint64_t> launches{0};
   std::string last_error;
-  // serving
+  // serving: the persistent request loop (pv_serve.cu)
   std::mutex mu;
-  DevBuf pool;
+  DevBuf pool;                          // request scratch, handed out by the arena
   Arena arena;
   bool pool_ready = false;
-  cudaStream_t serve_streams[kServeStreams] = {};
-  int next_stream = 0;
+  pvk::ServeCtl* sctl = nullptr;        // request ring (pinned host memory)
+  pvk::ServeCtl* sctl_dev = nullptr;    // its device address
+  pvk::ServeDev* sdev = nullptr;        // claim counter and per-slot counts (device)
+  cudaStream_t serve_stream = nullptr;
+  cudaEvent_t serve_end = nullptr;      // recorded after each launch of the kernel
+  bool serve_launched = false;
+  int serve_grid = 0;
+  unsigned int serve_epoch = 0;         // launches of the serving kernel so far
+  uint64_t published = 0;               // events published to the ring
+  uint64_t next_seq = 1;                // next admission number
+  uint64_t slot_cum[pvk::kServeRing] = {};
+  Request* slot_req[pvk::kServeRing] = {};
+  std::vector<Request*> inflight;       // admitted, not yet seen complete
+  int64_t clock_offset = 0;             // device global timer minus host steady clock, ns
   uint64_t next_ticket = 1;
   std::deque<Request*> pending;
   std::unordered_map<uint64_t, Request*> requests;
-  std::deque<uint64_t> retired_order;
 };
 
 namespace {
@@ -548,14 +560,24 @@ int run_staged(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, float* co
 
 // ---- serving internals (ctx->mu held) ------------------------------------
 
-size_t request_bytes(const pv_tracks* t, const pv_vertices* o) {
-  return FusedLayout(t->n_tracks, t->n_events, o->capacity).total;
-}
+// Scratch of one request in the pool: per track its center bin, vertex, place
+// in vertex order and fit inputs (31 bytes), each array 16-byte aligned.
+struct ServeLayout {
+  size_t center, cid, slot, A, W, total;
+  explicit ServeLayout(int64_t n) {
+    size_t o = 0;
+    A = o; o += round16(sizeof(float4) * n);
+    W = o; o += round16(sizeof(float2) * n);
+    slot = o; o += round16(sizeof(int32_t) * n);
+    center = o; o += round16(sizeof(int16_t) * n);
+    cid = o; o += round16(sizeof(int8_t) * n);
+    total = (o + 255) / 256 * 256;
+  }
+};
 
-void CUDART_CB on_request_done(void* arg) {
-  Request* r = static_cast<Request*>(arg);
-  r->t_done.store(now_ns());
-  r->done.store(1);
+uint64_t serve_idle_ns(const pv_ctx* ctx) {
+  const uint64_t lim = ctx->cfg.max_spin_ns ? ctx->cfg.max_spin_ns : 10000000000ull;
+  return lim < kServeIdleNs ? lim : kServeIdleNs;
 }
 
 int ensure_pool(pv_ctx* ctx) {
@@ -563,43 +585,132 @@ int ensure_pool(pv_ctx* ctx) {
   size_t bytes = ctx->cfg.pool_bytes ? ctx->cfg.pool_bytes : (size_t(1) << 30);
   PV_CUDA(ctx, ctx->pool.ensure(bytes));
   ctx->arena.reset(ctx->pool.bytes / 256 * 256);
-  for (int i = 0; i < kServeStreams; ++i)
-    PV_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->serve_streams[i], cudaStreamNonBlocking));
+  void* h = nullptr;
+  PV_CUDA(ctx, cudaHostAlloc(&h, sizeof(pvk::ServeCtl), cudaHostAllocMapped));
+  std::memset(h, 0, sizeof(pvk::ServeCtl));
+  ctx->sctl = static_cast<pvk::ServeCtl*>(h);
+  void* hd = nullptr;
+  PV_CUDA(ctx, cudaHostGetDevicePointer(&hd, h, 0));
+  ctx->sctl_dev = static_cast<pvk::ServeCtl*>(hd);
+  void* d = nullptr;
+  PV_CUDA(ctx, cudaMalloc(&d, sizeof(pvk::ServeDev)));
+  ctx->sdev = static_cast<pvk::ServeDev*>(d);
+  PV_CUDA(ctx, cudaMemset(d, 0, sizeof(pvk::ServeDev)));
+  PV_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking));
+  PV_CUDA(ctx, cudaEventCreateWithFlags(&ctx->serve_end, cudaEventDisableTiming));
+  const int per = pvk::serve_blocks_per_sm(ctx->C);
+  ctx->serve_grid = ctx->n_sm * (per > 0 ? per : 1);
+  // the device's global timer against the host clock: the stamp of a one-
+  // thread kernel against the midpoint of the host's readings around it (the
+  // closest of a few tries)
+  int64_t best = -1;
+  for (int i = 0; i < 5; ++i) {
+    const uint64_t t0 = now_ns();
+    PV_CUDA(ctx, pvk::launch_serve_clock(ctx->sctl_dev, ctx->serve_stream));
+    PV_CUDA(ctx, cudaStreamSynchronize(ctx->serve_stream));
+    const uint64_t t1 = now_ns();
+    const uint64_t g = *reinterpret_cast<volatile uint64_t*>(&ctx->sctl->clock_ns);
+    if (best < 0 || static_cast<int64_t>(t1 - t0) < best) {
+      best = static_cast<int64_t>(t1 - t0);
+      ctx->clock_offset = static_cast<int64_t>(g) - static_cast<int64_t>((t0 + t1) / 2);
+    }
+  }
+  ctx->sctl->exit_code = -1;
   ctx->pool_ready = true;
   return PV_OK;
 }
 
-// Launch a request on a serving stream with scratch from the arena.
-int launch_request(pv_ctx* ctx, Request* r) {
-  cudaStream_t st = ctx->serve_streams[r->stream];
-  char* base = static_cast<char*>(ctx->pool.p) + r->arena_off;
-  int rc = enqueue_fused(ctx, pvk::kFindFit, &r->tracks, nullptr, &r->out, base, st);
-  if (rc != PV_OK) return rc;
-  PV_CUDA(ctx, cudaLaunchHostFunc(st, on_request_done, r));
+// Writes request r into the next ring slot and publishes its events.
+void admit(pv_ctx* ctx, Request* r, size_t off) {
+  const uint64_t seq = ctx->next_seq++;
+  const int slot = static_cast<int>(seq % pvk::kServeRing);
+  pvk::ServeDesc* d = &ctx->sctl->ring[slot];
+  __atomic_store_n(&d->seq, ~0ull, __ATOMIC_RELEASE);
+  char* base = static_cast<char*>(ctx->pool.p) + off;
+  const ServeLayout L(r->tracks.n_tracks);
+  d->T = track_ptrs(&r->tracks);
+  d->O = out_ptrs(&r->out);
+  d->center = reinterpret_cast<int16_t*>(base + L.center);
+  d->cid = reinterpret_cast<int8_t*>(base + L.cid);
+  d->slot = reinterpret_cast<int32_t*>(base + L.slot);
+  d->A = reinterpret_cast<float4*>(base + L.A);
+  d->W = reinterpret_cast<float2*>(base + L.W);
+  d->ev_base = ctx->published;
+  ctx->slot_cum[slot] += static_cast<uint64_t>(r->tracks.n_events);
+  d->done_target = ctx->slot_cum[slot];
+  __atomic_store_n(&d->seq, seq, __ATOMIC_RELEASE);
+  ctx->published += static_cast<uint64_t>(r->tracks.n_events);
+  __atomic_store_n(&ctx->sctl->published, ctx->published, __ATOMIC_RELEASE);
+  r->arena_off = off;
+  r->seq = seq;
+  ctx->slot_req[slot] = r;
+}
+
+bool serve_running(pv_ctx* ctx) {
+  if (!ctx->serve_launched) return false;
+  const cudaError_t q = cudaEventQuery(ctx->serve_end);
+  if (q == cudaErrorNotReady) return true;
+  if (q != cudaSuccess) ctx->last_error = cudaGetErrorString(q);
+  ctx->serve_launched = false;
+  return false;
+}
+
+// Starts the serving kernel (if it is not running) from the oldest request
+// not yet complete.
+int start_server(pv_ctx* ctx) {
+  if (serve_running(ctx)) return PV_OK;
+  uint64_t start = ctx->next_seq;
+  for (const Request* r : ctx->inflight)
+    if (r->seq < start) start = r->seq;
+  // a new launch: its exit count and orphan list start empty, the previous
+  // launch's orphans wait to be taken
+  const unsigned int epoch = ++ctx->serve_epoch;
+  PV_CUDA(ctx, cudaMemsetAsync(&ctx->sdev->running, 0, sizeof(int), ctx->serve_stream));
+  PV_CUDA(ctx, cudaMemsetAsync(&ctx->sdev->orph_n[epoch & 1], 0, sizeof(int), ctx->serve_stream));
+  PV_CUDA(ctx, cudaMemsetAsync(&ctx->sdev->orph_take, 0, sizeof(int), ctx->serve_stream));
+  PV_CUDA(ctx, pvk::launch_serve(ctx->C, ctx->sctl_dev, ctx->sdev, serve_idle_ns(ctx), start, epoch,
+                                 ctx->serve_grid, ctx->serve_stream));
+  PV_CUDA(ctx, cudaEventRecord(ctx->serve_end, ctx->serve_stream));
+  ctx->serve_launched = true;
+  ctx->launches += 1;
   return PV_OK;
 }
 
-// Retire completed requests' memory and admit pending ones that now fit.
+// Retires completed requests (their pool memory returns to the arena), admits
+// waiting requests that fit (any of them: a large one at the head does not
+// block smaller ones behind it) and keeps the serving kernel running while
+// requests are in flight.
 int pump(pv_ctx* ctx) {
-  for (auto& kv : ctx->requests) {
-    Request* r = kv.second;
-    if (r->admitted && r->done.load() && r->bytes) {
+  size_t keep = 0;
+  for (size_t i = 0; i < ctx->inflight.size(); ++i) {
+    Request* r = ctx->inflight[i];
+    const int s = static_cast<int>(r->seq % pvk::kServeRing);
+    if (__atomic_load_n(&ctx->sctl->done_seq[s], __ATOMIC_ACQUIRE) == r->seq) {
+      const uint64_t g = *reinterpret_cast<volatile uint64_t*>(&ctx->sctl->done_ns[s]);
+      r->t_done = static_cast<uint64_t>(static_cast<int64_t>(g) - ctx->clock_offset);
+      if (r->t_done < r->t_submit) r->t_done = r->t_submit;
+      r->done = true;
       ctx->arena.release(r->arena_off, r->bytes);
-      r->bytes = 0;
+      ctx->slot_req[s] = nullptr;
+    } else {
+      ctx->inflight[keep++] = r;
     }
   }
-  while (!ctx->pending.empty()) {
-    Request* r = ctx->pending.front();
+  ctx->inflight.resize(keep);
+  bool in_flight = keep > 0;
+  for (auto it = ctx->pending.begin(); it != ctx->pending.end();) {
+    if (ctx->slot_req[ctx->next_seq % pvk::kServeRing]) break;   // ring full
     size_t off;
-    if (!ctx->arena.alloc(r->bytes, &off)) break;
-    r->arena_off = off;
-    r->admitted = true;
-    r->stream = ctx->next_stream;
-    ctx->next_stream = (ctx->next_stream + 1) % kServeStreams;
-    ctx->pending.pop_front();
-    int rc = launch_request(ctx, r);
-    if (rc != PV_OK) return rc;
+    if (!ctx->arena.alloc((*it)->bytes, &off)) {
+      ++it;
+      continue;
+    }
+    admit(ctx, *it, off);
+    ctx->inflight.push_back(*it);
+    in_flight = true;
+    it = ctx->pending.erase(it);
   }
+  if (in_flight) return start_server(ctx);
   return PV_OK;
 }
 
@@ -667,7 +778,7 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
   ctx->beam = b;
   ctx->C = C;
   if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-      pvk::fused_setup(C.nbins) != cudaSuccess) {
+      pvk::fused_setup(C.nbins) != cudaSuccess || pvk::serve_setup(C.nbins) != cudaSuccess) {
     delete ctx;
     return PV_ERR_CUDA;
   }
@@ -713,20 +824,24 @@ int pv_destroy(pv_ctx* ctx) {
     std::lock_guard<std::mutex> g(ctx->mu);
     uint64_t limit = ctx->cfg.max_spin_ns ? ctx->cfg.max_spin_ns : 10000000000ull;
     uint64_t t0 = now_ns();
-    // bounded wait for admitted requests; pending ones are dropped
-    for (;;) {
-      bool busy = false;
-      for (auto& kv : ctx->requests)
-        if (kv.second->admitted && !kv.second->done.load()) busy = true;
-      if (!busy) break;
+    // the serving kernel finishes the published requests, then sees the stop
+    // request; requests still waiting for admission are dropped
+    if (ctx->sctl) __atomic_store_n(&ctx->sctl->stop, 1u, __ATOMIC_RELEASE);
+    while (serve_running(ctx)) {
       if (now_ns() - t0 > limit) { rc = PV_ERR_TIMEOUT; break; }
       std::this_thread::yield();
     }
     if (rc == PV_OK) {
       for (auto& kv : ctx->requests) delete kv.second;
       ctx->requests.clear();
-      for (int i = 0; i < kServeStreams; ++i)
-        if (ctx->serve_streams[i]) cudaStreamDestroy(ctx->serve_streams[i]);
+      ctx->pending.clear();
+      ctx->inflight.clear();
+      if (ctx->serve_stream) cudaStreamDestroy(ctx->serve_stream);
+      if (ctx->serve_end) cudaEventDestroy(ctx->serve_end);
+      if (ctx->sctl) cudaFreeHost(ctx->sctl);
+      if (ctx->sdev) cudaFree(ctx->sdev);
+      ctx->sctl = nullptr;
+      ctx->sdev = nullptr;
     }
   }
   if (rc != PV_OK) return rc;   // leave the context alive: its requests still run
@@ -1068,7 +1183,7 @@ int pv_submit(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, uint64_t* 
   std::lock_guard<std::mutex> g(ctx->mu);
   rc = ensure_pool(ctx);
   if (rc != PV_OK) return rc;
-  size_t bytes = (request_bytes(tracks, out) + 255) / 256 * 256;
+  const size_t bytes = ServeLayout(tracks->n_tracks).total;
   if (bytes > ctx->arena.size) return PV_ERR_NOMEM;
   if (ctx->pending.size() >= kMaxQueued) {
     rc = pump(ctx);
@@ -1083,10 +1198,8 @@ int pv_submit(pv_ctx* ctx, const pv_tracks* tracks, pv_vertices* out, uint64_t* 
   r->bytes = bytes;
   r->t_submit = now_ns();
   if (tracks->n_events == 0) {
-    r->done.store(1);
-    r->t_done.store(r->t_submit);
-    r->admitted = true;
-    r->bytes = 0;
+    r->done = true;
+    r->t_done = r->t_submit;
   } else {
     ctx->pending.push_back(r);
   }
@@ -1101,8 +1214,8 @@ int pv_poll(pv_ctx* ctx, uint64_t ticket, int* done) {
   std::lock_guard<std::mutex> g(ctx->mu);
   auto it = ctx->requests.find(ticket);
   if (it == ctx->requests.end()) return PV_ERR_NOTFOUND;
-  int rc = pump(ctx);
-  *done = it->second->done.load();
+  int rc = it->second->done ? PV_OK : pump(ctx);
+  *done = it->second->done ? 1 : 0;
   return rc;
 }
 
@@ -1110,13 +1223,29 @@ int pv_request_latency_ns(pv_ctx* ctx, uint64_t ticket, uint64_t* ns) {
   if (!ctx || !ns) return PV_ERR_ARG;
   std::lock_guard<std::mutex> g(ctx->mu);
   auto it = ctx->requests.find(ticket);
-  if (it == ctx->requests.end() || !it->second->done.load()) return PV_ERR_NOTFOUND;
-  *ns = it->second->t_done.load() - it->second->t_submit;
-  // retire: its memory was returned to the arena by pump()
-  Request* r = it->second;
-  if (r->bytes) { ctx->arena.release(r->arena_off, r->bytes); r->bytes = 0; }
-  delete r;
+  if (it == ctx->requests.end() || !it->second->done) return PV_ERR_NOTFOUND;
+  *ns = it->second->t_done - it->second->t_submit;
+  delete it->second;
   ctx->requests.erase(it);
+  return PV_OK;
+}
+
+int pv_serve_start(pv_ctx* ctx) {
+  if (!ctx) return PV_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  int rc = ensure_pool(ctx);
+  if (rc != PV_OK) return rc;
+  return start_server(ctx);
+}
+
+int pv_serve_status(pv_ctx* ctx, int* running, int* last_exit) {
+  if (!ctx) return PV_ERR_ARG;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  const bool run = ctx->pool_ready && serve_running(ctx);
+  if (running) *running = run ? 1 : 0;
+  if (last_exit)
+    *last_exit = (ctx->sctl && !run) ? *reinterpret_cast<volatile int*>(&ctx->sctl->exit_code) : -1;
   return PV_OK;
 }
 

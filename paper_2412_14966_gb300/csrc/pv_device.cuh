@@ -24,9 +24,19 @@ namespace pvdev {
 #ifndef PV_CHECKED
 #define PV_CHECKED 0
 #endif
-#if PV_CHECKED && defined(__CUDA_ARCH__)
-__device__ void check_failed(unsigned code);
+#if PV_CHECKED
+// out-of-bounds indices met by the checked build: their number and the code
+// of the first one (one pair per translation unit, read by its report)
+static __device__ unsigned int g_check_count;
+static __device__ unsigned int g_check_first;
+#if defined(__CUDA_ARCH__)
+static __device__ __noinline__ void check_failed(unsigned code) {
+  if (atomicAdd(&g_check_count, 1u) == 0u) g_check_first = code;
+}
 #define PV_CHECK(cond, code) ((cond) ? true : (::pvdev::check_failed(code), false))
+#else
+#define PV_CHECK(cond, code) true
+#endif
 #else
 #define PV_CHECK(cond, code) true
 #endif
@@ -228,27 +238,16 @@ __device__ __forceinline__ void fill_template(uint32_t* hist, int tq, int j0, in
   }
 }
 
-// Warp-cooperative fill of the profiles of the 32 tracks held by the lanes
-// (one per lane; nb = 0 for a lane without a filled track).  Bin j0 + i of a
-// window [j0, j0 + nb) receives Q_{i+1} - Q_i with Q_0 = 0, Q_nb = ONE and Q_i
-// the quantised CDF at the bin edge j0 + i.  The running-max guard of
-// fill_profile is a no-op that is not repeated here: Q is non-decreasing along
-// a window because F is monotone on [-1, 1], every binary32 step of u and F is
-// a monotone rounding, and window edges are at least dz / (sqrt(5) sigma_max)
-// = 0.011 apart in u, far above the rounding error of F.  The histogram is
-// therefore the one fill_profile builds (integer adds commute).
-//
-// Two parts: every lane first adds the first kLaneItems bins of its own
-// window, carrying each right edge over as the next bin's left edge (one CDF
-// per bin, no exchange); the bins beyond those, of the wider windows, are
-// then spread over the lanes, 31 per pass: a lane finds its track by a
-// shuffle search over the prefix sums of the remaining bins, evaluates the CDF
-// at its bin's left edge and takes the right edge from the next lane (items of
-// one track sit in consecutive lanes, lane 31 only supplies an edge).  With
-// kProfile = TEMPLATE the CDF value at edge i is the class template's Q[i] (tq:
-// the class's start in q), and the histogram is the one fill_template builds.
-constexpr int kLaneItems = 4;
-
+// The quantised CDF value Q_i at edge i of a window starting at bin j0: the
+// cubic CDF at the bin edge j0 + i (inv = 1 / (sqrt(5) sigma_poca)), or with
+// kProfile = TEMPLATE the class template's Q[i] (tq: the class's start in q).
+// Bin j0 + i of a window of nb bins receives Q_{i+1} - Q_i with Q_0 = 0 and
+// Q_nb = ONE (fill_profile, fill_template).  Q is non-decreasing along a
+// window (F is monotone on [-1, 1], every binary32 step of u and F is a
+// monotone rounding, and window edges are at least dz / (sqrt(5) sigma_max) =
+// 0.011 apart in u, far above the rounding error of F), so the running-max
+// guard of fill_profile never acts and a fill that adds Q_{i+1} - Q_i per bin
+// in any order builds the same histogram (integer adds commute).
 template <int kProfile>
 __device__ __forceinline__ int profile_q(int i, int j0, float zpoca, float inv_s, int tq,
                                          const Consts& C) {
@@ -256,70 +255,6 @@ __device__ __forceinline__ int profile_q(int i, int j0, float zpoca, float inv_s
     return PV_CHECK(tq + i < kTplCap, 1) ? __ldg(C.tpl->q + tq + i) : 0;
   } else {
     return quant_cdf(__fmul_rn(__fsub_rn(edge_of(j0 + i, C), zpoca), inv_s));
-  }
-}
-
-template <int kProfile = PV_PROFILE_CUBIC>
-__device__ __forceinline__ void warp_fill_profiles(uint32_t* hist, float zpoca, float sigma,
-                                                   int j0, int nb, int tq, const Consts& C) {
-  const int lane = threadIdx.x & 31;
-  float inv_s = 0.0f;
-  if constexpr (kProfile != PV_PROFILE_TEMPLATE) {
-    float s = __fmul_rn(kSqrt5, sigma);
-    if (s < kSMin) s = 0.0f;
-    inv_s = (nb > 1 && s > 0.0f) ? __fdiv_rn(1.0f, s) : 0.0f;
-  }
-  // part 1: the lane's own first bins
-  {
-    int ql = 0;
-#pragma unroll
-    for (int i = 0; i < kLaneItems; ++i) {
-      if (i < nb) {
-        const int qr = (i + 1 < nb) ? profile_q<kProfile>(i + 1, j0, zpoca, inv_s, tq, C) : kOne;
-        const int w = qr - ql;
-        const int j = j0 + i;
-        if (w > 0 && j >= 0 && j < C.nbins && PV_CHECK(j < C.ntiles * 32, 2))
-          atomicAdd(hist + j, static_cast<uint32_t>(w));
-        ql = qr;
-      }
-    }
-  }
-  // part 2: the remaining bins of the wider windows, spread over the lanes
-  const int nr = nb > kLaneItems ? nb - kLaneItems : 0;
-  int incl = nr;                      // inclusive prefix of the remaining sizes
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  for (int base = 0; base < total; base += 31) {
-    const int idx = base + lane;
-    int L = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1)
-      if (__shfl_sync(0xffffffffu, incl, L + step - 1) <= idx) L += step;
-    const int o_incl = __shfl_sync(0xffffffffu, incl, L);
-    const int o_nb = __shfl_sync(0xffffffffu, nb, L);
-    const int o_j0 = __shfl_sync(0xffffffffu, j0, L);
-    // index in the window: the remaining bins start at kLaneItems
-    const int i = idx - (o_incl - (o_nb - kLaneItems)) + kLaneItems;
-    const int j = o_j0 + i;
-    int ql = 0;                       // quantised CDF at the left edge of bin j (i > 0)
-    if constexpr (kProfile == PV_PROFILE_TEMPLATE) {
-      const int o_tq = __shfl_sync(0xffffffffu, tq, L);
-      if (idx < total && PV_CHECK(o_tq + i < kTplCap, 1)) ql = __ldg(C.tpl->q + o_tq + i);
-    } else {
-      const float o_z = __shfl_sync(0xffffffffu, zpoca, L);
-      const float o_inv = __shfl_sync(0xffffffffu, inv_s, L);
-      if (idx < total) ql = quant_cdf(__fmul_rn(__fsub_rn(edge_of(j, C), o_z), o_inv));
-    }
-    const int qn = __shfl_down_sync(0xffffffffu, ql, 1);
-    const int qr = (i == o_nb - 1) ? kOne : qn;
-    const int w = qr - ql;
-    if (lane < 31 && idx < total && w > 0 && j >= 0 && j < C.nbins &&
-        PV_CHECK(j < C.ntiles * 32, 2))
-      atomicAdd(hist + j, static_cast<uint32_t>(w));
   }
 }
 
@@ -397,26 +332,21 @@ __host__ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t to
 // than its neighbours inside [a, b]; equal maxima by lower position; leftmost
 // minimum), split there when the dip is significant against the smaller
 // maximum and both sides hold the minimal integral, then the same on each
-// side.  Calls emit(lo, hi, integral, im) per piece in z order; total is the
-// integral of [a, b].  A range's first-found largest maximum is its argmax
-// (lowest index), and a side's integral is the parent's minus the other
-// side's, so a range costs one scan for its maxima plus the sum of its left
-// side.  Pieces come out in z order, so a pending right-hand side starts one
-// bin after the last piece emitted and only its last bin and integral wait on
-// the stack.  The stack holds kRecDepth entries; a deeper nesting (each
-// pending side holds at least the smaller minimal integral, so it needs a
-// proto-cluster of more than kRecDepth x 1.75 tracks' weight arranged as a
-// nested comb) emits the remaining range whole.
-constexpr int kRecDepth = 256;
-
+// side, to any depth.  Calls emit(lo, hi, integral, im) per piece in z order;
+// total is the integral of [a, b].  A range's first-found largest maximum is
+// its argmax (lowest index).  Pieces come out in z order, so every piece but
+// the last ends at the split point of the innermost pending right-hand side,
+// which starts one bin later: the pending sides need no stack, only their last
+// bin, kept in mark[] at their split point (mark: one int16 per histogram bin,
+// scratch; the proto-clusters of different lanes are disjoint).  A left side's
+// integral is summed while it is split off, a right side's during its maxima
+// scan.
 template <class Emit>
 __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64_t total,
-                                         const Consts& C, Emit&& emit) {
-  int16_t st_hi[kRecDepth];
-  uint64_t st_int[kRecDepth];
-  int sp = 0;
+                                         const Consts& C, Emit&& emit, int16_t* mark) {
   int lo = a, hi = b;
   uint64_t integral = total;
+  bool known = true;                  // integral of [lo, hi] known
   for (;;) {
     // one pass over the runs of equal bins (one load per bin): a run is a
     // maximum if the bins on both sides are lower (the range ends count as
@@ -426,9 +356,11 @@ __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64
     {
       int start = lo;
       uint32_t v = N[lo];
+      uint64_t sum = v;
       bool left_lower = true;
       for (int i = lo + 1; i <= hi + 1; ++i) {
         const uint32_t nv = i <= hi ? N[i] : 0u;
+        sum += nv;
         if (i > hi || nv != v) {
           if (left_lower && (i > hi || nv < v)) {
             if (m1 < 0 || v > v1) {
@@ -443,8 +375,9 @@ __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64
           v = nv;
         }
       }
+      if (!known) integral = sum;
     }
-    if (m2 >= 0 && sp < kRecDepth) {
+    if (m2 >= 0) {
       const int l = m1 < m2 ? m1 : m2, h = m1 < m2 ? m2 : m1;
       int m = -1;
       uint32_t vm = 0;
@@ -460,30 +393,29 @@ __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64
         for (int i = lo; i <= m; ++i) left += N[i];
         const uint64_t right = integral - left;
         if (left >= T && right >= T) {
-          st_hi[sp] = static_cast<int16_t>(hi);
-          st_int[sp] = right;
-          ++sp;
+          mark[m] = static_cast<int16_t>(hi);   // the pending side [m + 1, hi]
           hi = m;
           integral = left;
+          known = true;
           continue;
         }
       }
     }
     emit(lo, hi, integral, m1);
-    if (sp == 0) break;
-    --sp;
+    if (hi >= b) break;
     lo = hi + 1;
-    hi = st_hi[sp];
-    integral = st_int[sp];
+    hi = mark[hi];
+    known = false;
   }
 }
 
-// The pieces of proto-cluster [a, b] in the chosen flavour.
+// The pieces of proto-cluster [a, b] in the chosen flavour (mark: the
+// recursive split's per-bin scratch, unused by the z-order walk).
 template <int kSplit, class Emit>
 __host__ __device__ __forceinline__ void split_pieces(const uint32_t* N, int a, int b,
                                                       uint64_t total, const Consts& C,
-                                                      Emit&& emit) {
-  if constexpr (kSplit == PV_SPLIT_RECURSIVE) split_recursive(N, a, b, total, C, emit);
+                                                      Emit&& emit, int16_t* mark) {
+  if constexpr (kSplit == PV_SPLIT_RECURSIVE) split_recursive(N, a, b, total, C, emit, mark);
   else split_walk(N, a, b, total, C, emit);
 }
 
@@ -516,12 +448,15 @@ __device__ __forceinline__ uint32_t bin_or_zero(const uint32_t* N, int j, const 
 
 // Warp-cooperative peak search over a histogram N (shared or global).  If
 // tmask is non-null only tiles (32 bins) whose bit is set can hold non-zero
-// bins; otherwise every tile is scanned.  pc_lo / pc_hi are a kRunRing-entry ring
-// in shared memory.  Writes up to cap seeds into S in z order and returns the
-// number found (which may exceed cap).  All 32 lanes must call it.
+// bins; otherwise every tile is scanned.  pc_lo / pc_hi are a kRunRing-entry
+// ring in shared memory; mark (the recursive split's scratch, one int16 per
+// bin) is needed by that flavour only.  Writes up to cap seeds into S in z
+// order and returns the number found (which may exceed cap).  All 32 lanes
+// must call it.
 template <bool kSeedZ, int kSplit = PV_SPLIT_ZORDER>
 __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
-                                      SeedOut* S, int cap, int16_t* pc_lo, int16_t* pc_hi) {
+                                      SeedOut* S, int cap, int16_t* pc_lo, int16_t* pc_hi,
+                                      int16_t* mark = nullptr) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int n_seeds = 0;
@@ -545,12 +480,18 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
   };
   auto process = [&](int count) {
     // lane j walks proto-cluster n_done + j, counting the kept pieces and
-    // keeping the first one; only a lane with several kept pieces walks again
+    // keeping the first two; only a lane with three or more walks again
     int a = 0, b = -1;
     uint64_t total = 0;
     if (lane < count) {
       a = pc_lo[(n_done + lane) & (kRunRing - 1)];
       b = pc_hi[(n_done + lane) & (kRunRing - 1)];
+      // (a run's bounds always lie in the histogram; the test keeps a broken
+      // invariant from reading outside it)
+      if (!(a >= 0 && a <= b && b < C.nbins)) {
+        (void)PV_CHECK(false, 17);
+        b = a - 1;
+      }
       for (int i = a; i <= b; ++i) total += N[i];
     }
     // no piece of a proto-cluster can hold more than its total integral, so
@@ -558,7 +499,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     const uint64_t t_min = C.t_pp < C.t_gas ? C.t_pp : C.t_gas;
     const bool walk = lane < count && total >= t_min;
     int kept = 0, lo1 = 0, hi1 = 0, im1 = 0;
-    int lo2 = 0, hi2 = 0, im2 = 0;   // the first two kept pieces stay in registers
+    int lo2 = 0, hi2 = 0, im2 = 0;
     if (walk) {
       split_pieces<kSplit>(N, a, b, total, C, [&](int lo, int hi, uint64_t integral, int im) {
         if (keep_piece(integral, im, C)) {
@@ -569,7 +510,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
           }
           ++kept;
         }
-      });
+      }, mark);
     }
     int incl = kept;
     for (int o = 1; o < 32; o <<= 1) {
@@ -578,7 +519,6 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     }
     int n_kept = __shfl_sync(0xffffffffu, incl, 31);
     int pos = n_seeds + incl - kept;
-    // a proto-cluster with three or more kept pieces is walked again to write them
     if (kept >= 1 && kept <= 2 && pos < cap) {
       put(pos, lo1, hi1, im1);
       if (kept == 2 && pos + 1 < cap) put(pos + 1, lo2, hi2, im2);
@@ -589,13 +529,34 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
           if (pos < cap) put(pos, lo, hi, im);
           ++pos;
         }
-      });
+      }, mark);
     }
     n_seeds += n_kept;
     n_done += count;
     __syncwarp();
   };
 
+  // one tile: the starts and ends of the runs of bins above the threshold
+  // (the bins next to the tile come from the adjacent tiles)
+  auto scan_tile = [&](int q) {
+    const int bin = q * 32 + lane;
+    const uint32_t v = (bin < C.nbins) ? N[bin] : 0u;
+    const unsigned A = __ballot_sync(0xffffffffu, v > C.thr);
+    if (A == 0u) return;
+    const int bp = q * 32 - 1, bn = q * 32 + 32;
+    const unsigned pa = (bp >= 0 && bp < C.nbins && N[bp] > C.thr) ? 1u : 0u;
+    const unsigned na = (bn < C.nbins && N[bn] > C.thr) ? 0x80000000u : 0u;
+    const unsigned starts = A & ~((A << 1) | pa);
+    const unsigned ends = A & ~((A >> 1) | na);
+    if (starts & (1u << lane))
+      pc_lo[(n_starts + __popc(starts & lt)) & (kRunRing - 1)] = static_cast<int16_t>(bin);
+    if (ends & (1u << lane))
+      pc_hi[(n_ends + __popc(ends & lt)) & (kRunRing - 1)] = static_cast<int16_t>(bin);
+    n_starts += __popc(starts);
+    n_ends += __popc(ends);
+    __syncwarp();
+    while (n_ends - n_done >= 32) process(32);
+  };
 
   for (int w = 0; w < (C.ntiles + 31) / 32; ++w) {
     uint32_t m;
@@ -606,27 +567,9 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
       m = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
     }
     while (m) {
-      int tb = __ffs(m) - 1;
+      const int tb = __ffs(m) - 1;
       m &= m - 1;
-      const int q = w * 32 + tb;
-      int bin = q * 32 + lane;
-      const uint32_t v = (bin < C.nbins) ? N[bin] : 0u;
-      const unsigned A = __ballot_sync(0xffffffffu, v > C.thr);
-      if (A == 0u) continue;
-      // the bins next to the tile: the last of tile q - 1, the first of q + 1
-      const int bp = q * 32 - 1, bn = q * 32 + 32;
-      const unsigned pa = (bp >= 0 && bp < C.nbins && N[bp] > C.thr) ? 1u : 0u;
-      const unsigned na = (bn < C.nbins && N[bn] > C.thr) ? 0x80000000u : 0u;
-      const unsigned starts = A & ~((A << 1) | pa);
-      const unsigned ends = A & ~((A >> 1) | na);
-      if (starts & (1u << lane))
-        pc_lo[(n_starts + __popc(starts & lt)) & (kRunRing - 1)] = static_cast<int16_t>(bin);
-      if (ends & (1u << lane))
-        pc_hi[(n_ends + __popc(ends & lt)) & (kRunRing - 1)] = static_cast<int16_t>(bin);
-      n_starts += __popc(starts);
-      n_ends += __popc(ends);
-      __syncwarp();
-      while (n_ends - n_done >= 32) process(32);
+      scan_tile(w * 32 + tb);
     }
   }
   if (n_ends - n_done > 0) process(n_ends - n_done);

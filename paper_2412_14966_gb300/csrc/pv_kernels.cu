@@ -14,19 +14,7 @@
 // Plain path: one kernel per step (extrapolate / histogram / peaks /
 // associate / fit), one CTA per event, histograms and per-track state in
 // global memory: the per-step design the fused path is measured against.
-#include "pv_kernels.cuh"
-
-#if PV_CHECKED
-// out-of-bounds indices met by the checked build: their number and the code
-// of the first one
-__device__ unsigned int g_check_count;
-__device__ unsigned int g_check_first;
-namespace pvdev {
-__device__ void check_failed(unsigned code) {
-  if (atomicAdd(&g_check_count, 1u) == 0u) g_check_first = code;
-}
-}  // namespace pvdev
-#endif
+#include "pv_find.cuh"
 
 namespace pvk {
 
@@ -34,12 +22,16 @@ using namespace pvdev;
 
 bool check_report(unsigned* count, unsigned* first) {
 #if PV_CHECKED
-  unsigned zero = 0;
+  unsigned zero = 0, c = 0, f = 0;
   cudaDeviceSynchronize();
-  cudaMemcpyFromSymbol(count, g_check_count, sizeof(unsigned));
-  cudaMemcpyFromSymbol(first, g_check_first, sizeof(unsigned));
+  cudaMemcpyFromSymbol(&c, g_check_count, sizeof(unsigned));
+  cudaMemcpyFromSymbol(&f, g_check_first, sizeof(unsigned));
   cudaMemcpyToSymbol(g_check_count, &zero, sizeof(unsigned));
   cudaMemcpyToSymbol(g_check_first, &zero, sizeof(unsigned));
+  unsigned c2 = 0, f2 = 0;
+  serve_check_report(&c2, &f2);
+  *count = c + c2;
+  *first = c ? f : f2;
   return true;
 #else
   *count = 0;
@@ -48,61 +40,12 @@ bool check_report(unsigned* count, unsigned* first) {
 #endif
 }
 
-// ---------------------------------------------------------------------------
-// shared-memory layout of the find kernel
-
-struct Layout {
-  size_t hist, tmask, seeds, pc_lo, pc_hi, alive, part, cnt, voff, base, center, cid, misc, total;
-};
-
-__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-__host__ __device__ inline Layout make_layout(int nbins, int mode) {
-  Layout L;
-  size_t o = 0;
-  const bool find = (mode & kFind) != 0;
-  const int ntiles = (nbins + 31) / 32;
-  L.hist = o;   o += find ? sizeof(uint32_t) * ntiles * 32 : 0;
-  L.tmask = o;  o += sizeof(uint32_t) * kTileWords;
-  L.seeds = o;  o += align_up(sizeof(SeedOut), 16);
-  L.pc_lo = o;  o += sizeof(int16_t) * kRunRing;
-  L.pc_hi = o;  o += sizeof(int16_t) * kRunRing;
-  L.alive = o;  o += sizeof(int) * kMaxSeeds;
-  L.part = o;   o += sizeof(int) * kMaxSeeds;
-  L.cnt = o;    o += sizeof(int) * kMaxSeeds;
-  L.voff = o;   o += sizeof(int) * kMaxSeeds;
-  L.base = o;   o += sizeof(int) * kMaxSeeds;
-  L.misc = o;   o += sizeof(int) * 8;
-  L.center = o; o += sizeof(int16_t) * kSmallCap;
-  L.cid = o;    o += align_up(sizeof(int8_t) * kSmallCap, 16);
-  L.total = align_up(o, 16);
-  return L;
+size_t fused_smem_bytes(int nbins, int mode, int nt, bool rec) {
+  return make_layout(nbins, mode, nt, rec).total;
 }
-
-size_t fused_smem_bytes(int nbins, int mode) { return make_layout(nbins, mode).total; }
 
 // ---------------------------------------------------------------------------
 // pieces shared by the fused and the plain kernels
-
-// Exclusive scan of cnt[0..K) into voff and base (warp 0 only, K <= 64).
-__device__ __forceinline__ void warp_offsets(const int* cnt, int K, int* voff, int* base) {
-  const int lane = threadIdx.x & 31;
-  int c0 = lane < K ? cnt[lane] : 0;
-  int c1 = lane + 32 < K ? cnt[lane + 32] : 0;
-  int s0 = c0;
-  for (int o = 1; o < 32; o <<= 1) {
-    int v = __shfl_up_sync(0xffffffffu, s0, o);
-    if (lane >= o) s0 += v;
-  }
-  int tot0 = __shfl_sync(0xffffffffu, s0, 31);
-  int s1 = c1;
-  for (int o = 1; o < 32; o <<= 1) {
-    int v = __shfl_up_sync(0xffffffffu, s1, o);
-    if (lane >= o) s1 += v;
-  }
-  if (lane < K) { voff[lane] = s0 - c0; base[lane] = s0 - c0; }
-  if (lane + 32 < K) { voff[lane + 32] = tot0 + s1 - c1; base[lane + 32] = tot0 + s1 - c1; }
-}
 
 // Stable placement of tracks by vertex (track-index order inside a vertex);
 // warp 0 only.  base[] is advanced.
@@ -123,72 +66,6 @@ __device__ __forceinline__ void warp_slots(const int* cid, int n, int* base, int
     }
     __syncwarp();
   }
-}
-
-// The same placement for the fused path: slot[t] = position of track t among
-// its event's tracks in vertex order (SlotT: int16 in shared memory for small
-// events, int32 in global scratch above that); warp 0 only.
-template <typename CidT, typename SlotT>
-__device__ __forceinline__ void warp_place(const CidT* cid, int n, int* base, SlotT* slot) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int t0 = 0; t0 < n; t0 += 32) {
-    int t = t0 + lane;
-    int c = t < n ? static_cast<int>(cid[t]) : -1;
-    unsigned peers = __match_any_sync(0xffffffffu, c);
-    int rank = __popc(peers & lt);
-    int leader = __ffs(peers) - 1;
-    int b = c >= 0 ? base[c] : 0;
-    __syncwarp();
-    if (c >= 0) {
-      if (PV_CHECK(b + rank < n, 6)) slot[t] = static_cast<SlotT>(b + rank);
-      if (lane == leader) base[c] = b + __popc(peers);
-    }
-    __syncwarp();
-  }
-}
-
-// What group_fit returns for a vertex without tracks: singular at the first
-// iteration (or unconverged with no iteration when max_iter is 0).
-__device__ __forceinline__ VertexOut empty_fit(const Consts& C) {
-  VertexOut v;
-  v.x = v.y = v.z = 0.f;
-  for (int c = 0; c < 6; ++c) v.cov[c] = 0.f;
-  v.chi2 = 0.f;
-  v.ndof = -3.f;
-  v.n_tracks = 0;
-  v.n_iter = C.max_iter >= 1 ? 1 : 0;
-  v.status = C.max_iter >= 1 ? PV_ST_SINGULAR : PV_ST_MAXITER;
-  return v;
-}
-
-// Write the fit of vertex k of event e (result relative to the seed at
-// (xs, ys, zs)) with its selection status.
-__device__ __forceinline__ void write_vertex(const Consts& C, const OutPtrs& O, int e, int k,
-                                             float xs, float ys, float zs, const VertexOut& v) {
-  size_t q = static_cast<size_t>(e) * O.cap + k;
-  float x = xs + v.x, y = ys + v.y, z = zs + v.z;
-  int st = select_vertex(x, y, z, v.n_tracks, v.status, C);
-  O.x[q] = x;
-  O.y[q] = y;
-  O.z[q] = z;
-  if (O.cov) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) O.cov[q * 6 + c] = v.cov[c];
-  }
-  if (O.chi2) O.chi2[q] = v.chi2;
-  if (O.ndof) O.ndof[q] = v.ndof;
-  if (O.n_tracks) O.n_tracks[q] = v.n_tracks;
-  if (O.n_iter) O.n_iter[q] = v.n_iter;
-  if (O.status) O.status[q] = st;
-}
-
-// A seed without tracks gets the result of an empty fit at its seed
-// position.  Rare, and kept out of line so that its registers do not count
-// against the find kernel's occupancy.
-__device__ __noinline__ void write_empty_vertex(const Consts& C, const OutPtrs& O,
-                                                const SeedOut* S, int e, int k) {
-  write_vertex(C, O, e, k, S->x[k], S->y[k], S->z[k], empty_fit(C));
 }
 
 // Fit every vertex of one event (block-cooperative; used by the plain path).
@@ -226,310 +103,25 @@ __device__ __forceinline__ void block_fit_inputs(const TrackPtrs& T, int64_t b0,
   }
 }
 
-__device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tracks) {
-  return b0 < 0 || b1 < b0 || b1 > n_tracks || b1 - b0 > 0x7fffffffLL;
-}
-
-// ---------------------------------------------------------------------------
-// find kernel (fused path, stage 1)
-//
-// kFind:    steps (a)-(d1); outputs seeds and assignments.
-// kFindFit: the same, then fit inputs for every track (global scratch, vertex
-//           order) and one work item per vertex for the fit kernel; the seed
-//           position is left in the output row, which the fit overwrites.
-// kFit:     seeds and assignments from the caller, then fit inputs and work.
-
+// 48 registers per thread (a few bytes spill), so that ten 128-thread CTAs
+// share an SM: the shared memory of an event (22 KB) allows ten as well
 template <int MODE, int NT, int FLAV = 0>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 1280 / NT)
 find_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, TrackScratch G) {
-  constexpr int SPLIT = flavour_split(FLAV);
-  constexpr int PROFILE = flavour_profile(FLAV);
   extern __shared__ __align__(16) unsigned char smem[];
-  const Layout Lo = make_layout(C.nbins, MODE);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + Lo.hist);
-  uint32_t* tmask = reinterpret_cast<uint32_t*>(smem + Lo.tmask);
-  SeedOut* S = reinterpret_cast<SeedOut*>(smem + Lo.seeds);
-  int16_t* pc_lo = reinterpret_cast<int16_t*>(smem + Lo.pc_lo);
-  int16_t* pc_hi = reinterpret_cast<int16_t*>(smem + Lo.pc_hi);
-  int* alive = reinterpret_cast<int*>(smem + Lo.alive);
-  int* part = reinterpret_cast<int*>(smem + Lo.part);
-  int* cnt = reinterpret_cast<int*>(smem + Lo.cnt);
-  int* voff = reinterpret_cast<int*>(smem + Lo.voff);
-  int* base = reinterpret_cast<int*>(smem + Lo.base);
-  int16_t* s_center = reinterpret_cast<int16_t*>(smem + Lo.center);
-  int8_t* s_cid = reinterpret_cast<int8_t*>(smem + Lo.cid);
+  const Layout Lo = make_layout(C.nbins, MODE, NT, flavour_split(FLAV) == PV_SPLIT_RECURSIVE);
+  find_prologue<MODE, NT>(C, smem, Lo);
   int* misc = reinterpret_cast<int*>(smem + Lo.misc);
-
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int warp = tid >> 5;
-  constexpr int NW = NT / 32;
-
-  if (MODE & kFind) {
-    for (int i = tid; i < C.ntiles * 32; i += NT) hist[i] = 0u;
-  }
-  if (tid < kTileWords) tmask[tid] = 0u;
-  if (tid == 0) misc[0] = atomicAdd(G.counters, 1);
+  if (threadIdx.x == 0) misc[0] = atomicAdd(G.counters, 1);
   __syncthreads();
-
   for (int iter = 0;; ++iter) {
     const int e = misc[iter & 1];
     if (e >= T.n_events) break;
-    // the next event is claimed while this one runs, by the last warp (the
-    // one with the fewest tracks); the barrier that ends the iteration
-    // publishes it
+    // the next event is claimed while this one runs, by the last thread; the
+    // barrier after the fill publishes it
     int e_next = 0;
-    if (tid == NT - 1) e_next = atomicAdd(G.counters, 1);
-    const int64_t b0 = T.off[e], b1 = T.off[e + 1];
-    if (offsets_bad(b0, b1, T.n_tracks)) {
-      if (tid == 0) {
-        O.n_per_event[e] = 0;
-        if (O.event_status) O.event_status[e] = PV_EV_BAD_OFFSETS;
-      }
-      if (tid == NT - 1) misc[(iter + 1) & 1] = e_next;
-      __syncthreads();
-      continue;   // uniform: every thread read the same offsets
-    }
-    const int n = static_cast<int>(b1 - b0);
-    const bool small = n <= kSmallCap;
-    int16_t* center = small ? s_center : G.center + b0;
-    int8_t* cid = small ? s_cid : G.cid + b0;
-    int Ka = 0;
-
-    if (MODE & kFind) {
-      // (a) + (b): extrapolate, mark tiles, fill the shared histogram (one
-      // track per lane, then the warp's (track, bin) items spread over lanes)
-      // the inputs of a warp's next 32 tracks are loaded while the current
-      // ones are extrapolated and filled
-      // (kStage: the eight columns read here are also written to the device
-      // copy; the other three reach it by a copy alongside the kernel)
-      float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, r4 = 0.f, r5 = 0.f, r6 = 0.f, r7 = 0.f;
-      if (warp * 32 + lane < n) {
-        const int64_t i = b0 + warp * 32 + lane;
-        r0 = T.x[i]; r1 = T.y[i]; r2 = T.z[i]; r3 = T.tx[i];
-        r4 = T.ty[i]; r5 = T.cxx[i]; r6 = T.cxtx[i]; r7 = T.ctxtx[i];
-      }
-      for (int t0 = warp * 32; t0 < n; t0 += NT) {
-        const int t = t0 + lane;
-        const float c0 = r0, c1 = r1, c2 = r2, c3 = r3, c4 = r4, c5 = r5, c6 = r6, c7 = r7;
-        if constexpr ((MODE & kStage) != 0) {
-          if (t < n) {
-            const int64_t i = b0 + t;
-            G.stage[0][i] = c0; G.stage[1][i] = c1; G.stage[2][i] = c2; G.stage[3][i] = c3;
-            G.stage[4][i] = c4; G.stage[5][i] = c5; G.stage[6][i] = c6; G.stage[7][i] = c7;
-          }
-        }
-        if (t + NT < n) {
-          const int64_t i = b0 + t + NT;
-          r0 = T.x[i]; r1 = T.y[i]; r2 = T.z[i]; r3 = T.tx[i];
-          r4 = T.ty[i]; r5 = T.cxx[i]; r6 = T.cxtx[i]; r7 = T.ctxtx[i];
-        }
-        if constexpr ((MODE & kFit) != 0 && (MODE & kStage) == 0) {
-          // the fit-input pass reads the three y-covariance columns: bring
-          // this round's into L2 now
-          if (t < n) {
-            const int64_t i = b0 + t;
-            prefetch_l2(T.cyy + i);
-            prefetch_l2(T.cyty + i);
-            prefetch_l2(T.ctyty + i);
-          }
-        }
-        Prep p;
-        p.filled = false;
-        p.zpoca = p.sigma = 0.0f;
-        p.j0 = 0;
-        p.j1 = -1;
-        p.tq = 0;
-        if (t < n) {
-          p = prepare_track<PROFILE>(c0, c1, c2, c3, c4, c5, c6, c7, C);
-          if (PV_CHECK(!small || t < kSmallCap, 7))
-            center[t] = static_cast<int16_t>(p.filled ? p.center : -1);
-        }
-        {
-          // the 32-bin tiles the windows touch: each lane's range as four
-          // mask words, OR-reduced over the warp, one atomic per new word
-          int q0 = 1, q1 = 0;
-          if (p.filled) {
-            q0 = (p.j0 < 0 ? 0 : p.j0) >> 5;
-            q1 = (p.j1 >= C.nbins ? C.nbins - 1 : p.j1) >> 5;
-          }
-#pragma unroll
-          for (int w = 0; w < kTileWords; ++w) {
-            const int lo = q0 > 32 * w ? q0 : 32 * w;
-            const int hi = q1 < 32 * w + 31 ? q1 : 32 * w + 31;
-            uint32_t m = 0u;
-            if (lo <= hi) {
-              const int len = hi - lo + 1;
-              m = (len == 32 ? 0xffffffffu : ((1u << len) - 1u)) << (lo - 32 * w);
-            }
-            m = __reduce_or_sync(0xffffffffu, m);
-            if (lane == w && m != 0u && (tmask[w] & m) != m) atomicOr(tmask + w, m);
-          }
-        }
-        warp_fill_profiles<PROFILE>(hist, p.zpoca, p.sigma, p.j0,
-                                    p.filled ? p.j1 - p.j0 + 1 : 0, p.tq, C);
-      }
-      if (tid == NT - 1) misc[(iter + 1) & 1] = e_next;
-      __syncthreads();
-      // (c): seeds from the touched tiles (warp 0)
-      if (warp == 0) {
-        // (the seed positions are computed after the association, for the
-        // surviving seeds only)
-        int K = warp_find_seeds<false, SPLIT>(hist, tmask, C, S, O.cap, pc_lo, pc_hi);
-        if (lane == 0) misc[2] = K;
-      }
-      __syncthreads();
-      const int Kall = misc[2];
-      const int K = Kall < O.cap ? Kall : O.cap;
-      // clear the touched tiles for the next event (warp w the tiles of mask
-      // word w, w + NW, ...)
-      for (int w = warp; w < kTileWords; w += NW) {
-        uint32_t m = tmask[w];
-        while (m) {
-          const int tb = __ffs(m) - 1;
-          m &= m - 1;
-          hist[(w * 32 + tb) * 32 + lane] = 0u;
-        }
-      }
-      // (d1): association with the removal loop
-      Ka = block_associate(center, cid, n, S, K, C, alive, part, cnt, misc + 3);
-      if (tid < kTileWords) tmask[tid] = 0u;
-      // seed positions of the survivors: z from the bins around the maximum
-      // in binary64 (Sec. 3.3, R9), x and y on the beamline
-      if (tid < Ka) {
-        const float zs = seed_z_from(S->nm[tid], S->ni[tid], S->np[tid], S->bin[tid], C);
-        S->z[tid] = zs;
-        S->x[tid] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
-        S->y[tid] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));
-      }
-      __syncthreads();
-      for (int t = tid; t < n; t += NT) O.track_vertex[b0 + t] = cid[t];
-      if (tid == 0) {
-        O.n_per_event[e] = Ka;
-        if (O.event_status) O.event_status[e] = Kall > O.cap ? PV_EV_SEED_OVERFLOW : 0;
-      }
-      if (tid < Ka) {
-        size_t q = static_cast<size_t>(e) * O.cap + tid;
-        if (O.bin_lo) O.bin_lo[q] = S->lo[tid];
-        if (O.bin_hi) O.bin_hi[q] = S->hi[tid];
-        if (O.bin_max) O.bin_max[q] = S->bin[tid];
-        if (MODE == kFind) {
-          O.x[q] = S->x[tid];
-          O.y[q] = S->y[tid];
-          O.z[q] = S->z[tid];
-        }
-      }
-    } else {
-      // fit only: seeds and assignment from the caller
-      int K = SP.n_per_event[e];
-      int capk = SP.cap < O.cap ? SP.cap : O.cap;
-      capk = capk < kMaxSeeds ? capk : kMaxSeeds;
-      K = K < 0 ? 0 : (K > capk ? capk : K);
-      if (tid < K) {
-        size_t q = static_cast<size_t>(e) * SP.cap + tid;
-        S->x[tid] = SP.x[q];
-        S->y[tid] = SP.y[q];
-        S->z[tid] = SP.z[q];
-        S->bin[tid] = -1;             // the seed is given, not a histogram maximum
-        cnt[tid] = 0;
-      }
-      __syncthreads();
-      for (int t = tid; t < n; t += NT) {
-        int c = SP.track_vertex[b0 + t];
-        c = (c >= 0 && c < K) ? c : -1;
-        cid[t] = static_cast<int8_t>(c);
-        if (c >= 0) atomicAdd(cnt + c, 1);
-        if (O.track_vertex != SP.track_vertex) O.track_vertex[b0 + t] = c;
-      }
-      if (tid == 0 && O.n_per_event != SP.n_per_event) O.n_per_event[e] = K;
-      Ka = K;
-      if (tid == NT - 1) misc[(iter + 1) & 1] = e_next;
-      __syncthreads();
-    }
-
-    if (MODE & kFit) {
-      // each track's place in vertex order, one work item per vertex with
-      // tracks (a vertex without tracks gets the singular result of an empty
-      // fit here), then every track's fit inputs at its vertex's seed,
-      // written in vertex order for the fit kernel
-      if (warp == 0) warp_offsets(cnt, Ka, voff, base);
-      __syncthreads();
-      // after the association the center bins are spent: small events keep
-      // their slots in the same shared array
-      int16_t* s_slot = s_center;
-      if (warp == 0) {
-        if (small) warp_place(cid, n, base, s_slot);
-        else warp_place(cid, n, base, G.slot + b0);
-      } else if (warp == 1) {
-        // one work item per vertex with tracks, in the list of its size class
-        const unsigned lt = (1u << lane) - 1u;
-        const int c0 = (lane < Ka && cnt[lane] > 0) ? work_class(cnt[lane]) : -1;
-        const int c1 = (lane + 32 < Ka && cnt[lane + 32] > 0) ? work_class(cnt[lane + 32]) : -1;
-        // per class: lane c reserves the class's entries (one round trip for
-        // all classes), then each vertex takes its rank within its class
-        int mine = 0;
-#pragma unroll 1
-        for (int c = 0; c < kWorkClasses; ++c) {
-          const int k = __popc(__ballot_sync(0xffffffffu, c0 == c)) +
-                        __popc(__ballot_sync(0xffffffffu, c1 == c));
-          if (lane == c) mine = k;
-        }
-        int wb = 0;
-        if (lane < kWorkClasses && mine > 0) wb = atomicAdd(G.counters + 1 + lane, mine);
-        int i0 = 0, i1 = 0;
-#pragma unroll 1
-        for (int c = 0; c < kWorkClasses; ++c) {
-          const unsigned m0 = __ballot_sync(0xffffffffu, c0 == c);
-          const unsigned m1 = __ballot_sync(0xffffffffu, c1 == c);
-          const int bc = __shfl_sync(0xffffffffu, wb, c);
-          if (c0 == c) i0 = bc + __popc(m0 & lt);
-          if (c1 == c) i1 = bc + __popc(m0) + __popc(m1 & lt);
-        }
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-          const int k = lane + 32 * h;
-          if (k >= Ka) continue;
-          const int cl = h ? c1 : c0;
-          const int idx = h ? i1 : i0;
-          if (cl >= 0) {
-            if (idx < class_pick(G.cls_cap, cl)) {
-              VertexWork w;
-              w.off = static_cast<int>(b0 + voff[k]);
-              w.e = e;
-              w.kc = k | (cnt[k] << 8);
-              w.pad0 = 0;
-              w.x = __float_as_uint(S->x[k]);
-              w.y = __float_as_uint(S->y[k]);
-              w.z = __float_as_uint(S->z[k]);
-              w.pad1 = 0;
-              if (PV_CHECK(idx >= 0, 9)) G.work[class_pick(G.cls_base, cl) + idx] = w;
-            }
-          } else {
-            write_empty_vertex(C, O, S, e, k);
-          }
-        }
-      }
-      __syncthreads();
-      // fit inputs (the staged mode reads its first eight columns back from
-      // the device copy the fill wrote, the other three from host memory)
-      for (int t = tid; t < n; t += NT) {
-        const int c = static_cast<int>(cid[t]);
-        if (c < 0) continue;
-        const int sl = small ? static_cast<int>(s_slot[t]) : G.slot[b0 + t];
-        if (!PV_CHECK(sl >= 0 && sl < n && c < kMaxSeeds, 10)) continue;
-        const int64_t i = b0 + t;
-        float x, y, z, tx, ty, cxx, cxtx, ctxtx;
-        if constexpr ((MODE & kStage) != 0) {
-          x = G.stage[0][i]; y = G.stage[1][i]; z = G.stage[2][i]; tx = G.stage[3][i];
-          ty = G.stage[4][i]; cxx = G.stage[5][i]; cxtx = G.stage[6][i]; ctxtx = G.stage[7][i];
-        } else {
-          x = T.x[i]; y = T.y[i]; z = T.z[i]; tx = T.tx[i];
-          ty = T.ty[i]; cxx = T.cxx[i]; cxtx = T.cxtx[i]; ctxtx = T.ctxtx[i];
-        }
-        make_fit_track(x, y, z, tx, ty, cxx, cxtx, ctxtx, T.cyy[i], T.cyty[i], T.ctyty[i],
-                       S->x[c], S->y[c], S->z[c], G.A + b0 + sl, G.W + b0 + sl);
-      }
-    }
+    if (threadIdx.x == NT - 1) e_next = atomicAdd(G.counters, 1);
+    find_event<MODE, NT, FLAV>(C, T, SP, O, G, smem, e, misc + ((iter + 1) & 1), e_next);
     __syncthreads();   // shared state is reused by the next event
   }
 }
@@ -958,7 +550,7 @@ template <int MODE, int NT, int FLAV>
 static cudaError_t setup_find_flav(int nbins) {
   cudaError_t err = cudaFuncSetAttribute(find_kernel<MODE, NT, FLAV>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fused_smem_bytes(nbins, MODE));
+                                         (int)fused_smem_bytes(nbins, MODE, NT, flavour_split(FLAV) == PV_SPLIT_RECURSIVE));
   if (err != cudaSuccess) return err;
   return cudaFuncSetAttribute(find_kernel<MODE, NT, FLAV>,
                               cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1004,7 +596,7 @@ template <int MODE, int NT, int FLAV = 0>
 static int find_blocks(int nbins) {
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, find_kernel<MODE, NT, FLAV>, NT,
-                                                    fused_smem_bytes(nbins, MODE)) != cudaSuccess)
+                                                    fused_smem_bytes(nbins, MODE, NT, flavour_split(FLAV) == PV_SPLIT_RECURSIVE)) != cudaSuccess)
     return 0;
   return blocks;
 }
@@ -1096,7 +688,10 @@ static void launch_find(int nt, int grid, size_t sm, cudaStream_t st, const Cons
 cudaError_t launch_fused(int mode, const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
                          const OutPtrs& O, const TrackScratch& ws, const LaunchCfg& L,
                          cudaStream_t st, int* n_launches) {
-  size_t sm = fused_smem_bytes(C.nbins, mode);
+  // the x86 flavours of the find are built at kFlavThreads only
+  const int nt = (mode != kFit && flavour_of(C) != 0) ? kFlavThreads : L.find_nt;
+  size_t sm = fused_smem_bytes(C.nbins, mode & ~kStage, nt,
+                               mode != kFit && C.split_mode == PV_SPLIT_RECURSIVE);
   cudaError_t err = cudaMemsetAsync(ws.counters, 0, kCounterInts * sizeof(int), st);
   if (err != cudaSuccess) return err;
   if (mode == kFindFitStaged) {
@@ -1235,6 +830,7 @@ plain_peaks_kernel(Consts C, TrackPtrs T, const uint32_t* hist, int cap, int32_t
                    int32_t* ev_status) {
   __shared__ SeedOut S;
   __shared__ int16_t pc_lo[kRunRing], pc_hi[kRunRing];
+  __shared__ int16_t mark[SPLIT == PV_SPLIT_RECURSIVE ? kMaxBins : 1];
   const int e = blockIdx.x;
   const int64_t b0 = T.off[e], b1 = T.off[e + 1];
   const int lane = threadIdx.x;
@@ -1243,7 +839,7 @@ plain_peaks_kernel(Consts C, TrackPtrs T, const uint32_t* hist, int cap, int32_t
     return;
   }
   int K = warp_find_seeds<true, SPLIT>(hist + static_cast<size_t>(e) * C.nbins, nullptr, C, &S,
-                                       cap, pc_lo, pc_hi);
+                                       cap, pc_lo, pc_hi, mark);
   int Ks = K < cap ? K : cap;
   for (int k = lane; k < Ks; k += 32) {
     size_t q = static_cast<size_t>(e) * kMaxSeeds + k;

@@ -79,7 +79,9 @@ __host__ __device__ __forceinline__ V class_pick(const V (&a)[kWorkClasses], int
   return c == 0 ? a[0] : (c == 1 ? a[1] : (c == 2 ? a[2] : a[3]));
 }
 
-enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3, kStage = 4 };
+enum Mode : int { kFind = 1, kFit = 2, kFindFit = 3, kStage = 4, kServe = 8 };
+// kFindFit | kServe: the serving kernel's event work, which fits the event's
+// vertices in the same CTA instead of listing them for the fit kernel
 // kFindFit | kStage: the tracks are in host memory the device can address; the
 // find kernel reads every column there once: the eight its steps (a)-(b) need
 // in the fill, writing them to a device copy (TrackScratch::stage) that its
@@ -128,7 +130,7 @@ struct PlainScratch {
   int32_t* ev_status;    // [n_events]
 };
 
-size_t fused_smem_bytes(int nbins, int mode);
+size_t fused_smem_bytes(int nbins, int mode, int nt, bool rec);
 cudaError_t fused_setup(int nbins);
 
 // Launch shape of the fused path (block sizes and persistent grids); results do
@@ -147,6 +149,8 @@ cudaError_t launch_fused(int mode, const pvdev::Consts& C, const TrackPtrs& T, c
 // The checked build's record of out-of-bounds indices (count, first code),
 // reset by the call; false in the default build, which has no checks.
 bool check_report(unsigned* count, unsigned* first);
+// The same record of the serving kernel's translation unit.
+bool serve_check_report(unsigned* count, unsigned* first);
 
 bool find_block_ok(int nt);
 bool fit_block_ok(int ft);
@@ -169,6 +173,70 @@ inline long long class_capacity(int c, long long n_tracks, long long n_events, i
   long long by_tracks = n_tracks / kClassMinTracks[c];
   return by_tracks < all ? by_tracks : all;
 }
+
+// ---------------------------------------------------------------------------
+// Serving: the persistent request loop.  The host writes one descriptor per
+// admitted request into a ring in pinned host memory the device reads
+// (ServeCtl, mapped), then publishes the request's events by raising
+// `published`; the events of all requests form one sequence, request r owning
+// [ev_base, ev_base + n_events).  The serving kernel's CTAs claim events of
+// that sequence one at a time, run the find and the fit of each, and the CTA
+// that completes a request's last event stamps done_ns (the GPU's global
+// timer) and done_seq in the ring.  A CTA whose claimed event is not
+// published within idle_ns ends; the kernel ends when all have (exit code
+// PV_ERR_TIMEOUT), or PV_OK after the host sets `stop`.
+constexpr int kServeRing = 1024;
+constexpr int kServeThreads = 128;
+
+struct ServeDesc {
+  TrackPtrs T;                       // the request's device tracks
+  OutPtrs O;                         // its device outputs
+  int16_t* center;                   // its scratch (events above kSmallCap tracks)
+  int8_t* cid;
+  int32_t* slot;
+  float4* A;                         // its fit inputs in vertex order
+  float2* W;
+  unsigned long long ev_base;        // its first event in the sequence
+  unsigned long long done_target;    // ServeDev::slot_done of its slot when complete
+  unsigned long long seq;            // request number, written last (~0: being written)
+};
+
+struct ServeCtl {                    // pinned host memory, mapped for the device
+  unsigned long long published;      // events published so far (host)
+  unsigned int stop;                 // host: end the kernel
+  int exit_code;                     // device: why the kernel ended
+  unsigned long long exit_ns;        // device: global timer at the end
+  unsigned long long clock_ns;       // device: global timer (clock calibration)
+  unsigned long long done_seq[kServeRing];   // device: last request completed in a slot
+  unsigned long long done_ns[kServeRing];    // device: its completion time
+  ServeDesc ring[kServeRing];
+};
+
+// Events are claimed with one atomic add each, so a CTA with nothing to do
+// holds the next unpublished event and waits for it; if its wait runs out it
+// hands the event to the next launch of the kernel through the orphan list of
+// its launch (epoch & 1), which that launch takes first.
+constexpr int kServeOrphans = 4096;  // at least the largest grid
+
+struct ServeDev {                    // device memory
+  unsigned long long next_event;     // next event of the sequence to claim
+  unsigned long long slot_done[kServeRing];  // events completed per slot, cumulative
+  int running;                       // CTAs that left the loop (this launch)
+  int orph_n[2];                     // events handed on, per launch parity
+  int orph_take;                     // orphans of the previous launch taken so far
+  unsigned long long orph[2][kServeOrphans];
+};
+
+// Launches the serving kernel (grid = SMs x resident CTAs) on st; it reads
+// requests from seq_start on.  The flavour and accumulation mode come from C.
+cudaError_t launch_serve(const pvdev::Consts& C, ServeCtl* ctl, ServeDev* dev,
+                         unsigned long long idle_ns, unsigned long long seq_start,
+                         unsigned int epoch, int grid, cudaStream_t st);
+// Resident CTAs per SM of the serving kernel; its dynamic shared memory.
+int serve_blocks_per_sm(const pvdev::Consts& C);
+cudaError_t serve_setup(int nbins);
+// Writes the device's global timer to ctl->clock_ns (one thread).
+cudaError_t launch_serve_clock(ServeCtl* ctl, cudaStream_t st);
 
 // Multi-vertex fit (GPU flavour of Sec. 3.5) of the seeds S into O.
 struct MvLastState {        // the sheared position a vertex's last weights were taken at

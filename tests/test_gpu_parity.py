@@ -426,3 +426,48 @@ def test_run_host_pipeline_equals_device_path(pv, case):
     assert np.array_equal(o["track_vertex"][:nt][owned], v["track_vertex"][:nt][owned])
     if case == "unsplittable":
         assert o["event_status"][E - 1] == pv.EV_BAD_OFFSETS
+
+
+def _comb_event(n_peaks=40, rising=True):
+    """One event whose histogram is a single proto-cluster of n_peaks narrow
+    peaks (k + 3 tracks each, one bin wide, 1 mm apart in the p-gas region) on
+    a floor of 24 broad tracks: rising to the right, the recursive split (the
+    two largest maxima are the two rightmost peaks at every level) nests
+    n_peaks - 1 pending right-hand sides."""
+    ev = []
+    t = np.array([[0.3, 0.0]])
+    for k in range(n_peaks):
+        z = -450.0 + k * 1.0 + 0.125
+        m = (k if rising else n_peaks - 1 - k) + 3
+        ev.append(synthetic.straight_tracks((0.0, 0.0, z), np.repeat(t, m, 0), np.full(m, z),
+                                            cov_xx=(0.02 * 0.3) ** 2, cov_tt=1e-14))
+    for j in range(24):
+        z = -462.0 + 2.5 * j
+        ev.append(synthetic.straight_tracks((0.0, 0.0, z), t, [z], cov_xx=(8.0 * 0.3) ** 2,
+                                            cov_tt=1e-14))
+    return {k: np.concatenate([e[k] for e in ev]) for k in synthetic.TRACK_FIELDS}
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_recursive_split_deep_comb_on_the_gpu(pv, path):
+    """The x86 flavour's recursive split to depth 39 on the device (and a
+    falling comb, which splits at the top level every time): seeds, bounds and
+    assignments bit-exact with the oracle, every peak a seed."""
+    batch = synthetic.batch_from_events([_comb_event(), _comb_event(rising=False),
+                                         _comb_event(25)])
+    p = oracle.default_params(split_mode=1)
+    ref = oracle.find_batch(batch, p, want_hist=True)
+    # each comb is one proto-cluster: every bin from its first to its last
+    # peak is above the threshold
+    for e, npk in enumerate((40, 40, 25)):
+        h = ref["hist"][e]
+        assert ref["n"][e] == npk
+        lo, hi = ref["lo"][e, 0], ref["hi"][e, npk - 1]
+        assert np.all(h[lo:hi + 1] > p.bin_threshold), e
+    cfg = dict(split_mode=pv.SPLIT_RECURSIVE)
+    if path == "plain":
+        cfg["path"] = pv.PATH_PLAIN
+    ctx = pv.Context(device=0, **cfg)
+    s, v = G.gpu_find_fit(ctx, batch)
+    ctx.close()
+    G.assert_find_equal(s, ref, batch)

@@ -1,6 +1,9 @@
 """Serving through pv_submit / pv_poll: requests of uneven size are admitted as
-the device memory pool frees up, run concurrently on the serving streams, and
-every result is bit-identical to the same request run alone."""
+the device memory pool frees up, their events run side by side in the
+persistent serving kernel, and every result is bit-identical to the same
+request run alone.  The serving kernel's wait for work is bounded: with
+nothing submitted it ends on its own (PV_ERR_TIMEOUT) and the context stays
+usable."""
 import time
 
 import numpy as np
@@ -126,6 +129,61 @@ def test_interleaved_submit_and_poll_keeps_results():
                 live.remove((j, tk))
                 done.append(j)
     _wait(ctx, [tk for _, tk in live])
+    torch.cuda.synchronize()
+    for (b, _), o, r in zip(reqs, outs, ref):
+        _same(o.numpy(), r, b)
+    ctx.close()
+
+
+def test_idle_server_ends_on_its_own_and_the_context_stays_usable():
+    """A serving kernel started with no request waits for work at most its idle
+    bound (here max_spin_ns = 0.2 ms), then ends with PV_ERR_TIMEOUT; a request
+    submitted afterwards starts it again and completes with the batched
+    path's results."""
+    import torch
+
+    import paper_2412_14966_gb300 as pv
+    ctx = pv.Context(device=0, max_spin_ns=200_000)
+    ctx.serve_start()
+    t0 = time.time()
+    while True:
+        running, last = ctx.serve_status()
+        if not running:
+            break
+        assert time.time() - t0 < 10.0, "serving kernel did not end"
+        time.sleep(0.001)
+    assert last == pv.PV_ERR_TIMEOUT
+    b = synthetic.workload_mixture(n_events=300, seed=11)
+    t = pv.Tracks.from_batch(b)
+    ref_ctx = pv.Context(device=0)
+    ref = ref_ctx.fit_batch(t).numpy()
+    ref_ctx.close()
+    o = pv.Vertices.empty(b.n_events, b.n_tracks)
+    tk = ctx.submit(t, o)
+    _wait(ctx, [tk])
+    torch.cuda.synchronize()
+    _same(o.numpy(), ref, b)
+    assert ctx.latency_ns(tk) > 0
+    ctx.close()
+
+
+def test_serving_follows_the_context_settings():
+    """The serving kernel runs the context's flavour and accumulation mode:
+    x86 flavour with binary64 sums, bit-identical to the batched path."""
+    import torch
+
+    import paper_2412_14966_gb300 as pv
+    cfg = dict(split_mode=pv.SPLIT_RECURSIVE, profile_mode=pv.PROFILE_TEMPLATE,
+               accum_mode=pv.ACCUM_FP64)
+    reqs = _requests(pv, 6, seed=13)
+    alone = pv.Context(device=0, **cfg)
+    ref = [alone.fit_batch(t).numpy() for _, t in reqs]
+    torch.cuda.synchronize()
+    alone.close()
+    ctx = pv.Context(device=0, **cfg)
+    outs = [pv.Vertices.empty(b.n_events, b.n_tracks) for b, _ in reqs]
+    tickets = [ctx.submit(t, o) for (b, t), o in zip(reqs, outs)]
+    _wait(ctx, tickets)
     torch.cuda.synchronize()
     for (b, _), o, r in zip(reqs, outs, ref):
         _same(o.numpy(), r, b)

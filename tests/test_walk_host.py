@@ -181,3 +181,17 @@ def test_recursive_split_deep_comb(harness):
     rec = _gpu_walk(harness, h, 1)
     assert rec == _oracle(h, P_REC)
     assert len(rec) == 40
+
+
+def test_recursive_split_deeper_than_any_fixed_stack(harness):
+    """A comb of 600 peaks rising to the right in one proto-cluster nests 599
+    pending right-hand sides (the split keeps them at their split points, so
+    no depth is too deep); every peak becomes a seed, as in the oracle."""
+    vals = []
+    for k in range(600):
+        vals += [9000 + 10 * k, 3000, 300]
+    h = _hist(20, vals[:-1])
+    assert int(np.count_nonzero(h)) < NB
+    rec = _gpu_walk(harness, h, 1)
+    assert rec == _oracle(h, P_REC)
+    assert len(rec) == 600

@@ -3,6 +3,7 @@
 // many histograms.  Test code only: proto-clusters are found with a plain loop
 // and every proto-cluster is walked (no early skip).
 #include <cstdint>
+#include <vector>
 
 #include "pv_device.cuh"
 
@@ -18,6 +19,7 @@ extern "C" int harness_seeds(const uint32_t* N, int nbins, uint32_t thr, uint32_
   C.dip_den = dip_den;
   C.gas_bin = gas_bin;
   int n = 0;
+  std::vector<int16_t> mark(nbins);   // the recursive split's per-bin scratch
   for (int i = 0; i < nbins; ++i) {
     if (!(N[i] > thr)) continue;
     const int a = i;
@@ -36,9 +38,9 @@ extern "C" int harness_seeds(const uint32_t* N, int nbins, uint32_t thr, uint32_
       }
     };
     if (split_mode == PV_SPLIT_RECURSIVE)
-      pvdev::split_pieces<PV_SPLIT_RECURSIVE>(N, a, b, total, C, emit);
+      pvdev::split_pieces<PV_SPLIT_RECURSIVE>(N, a, b, total, C, emit, mark.data());
     else
-      pvdev::split_pieces<PV_SPLIT_ZORDER>(N, a, b, total, C, emit);
+      pvdev::split_pieces<PV_SPLIT_ZORDER>(N, a, b, total, C, emit, mark.data());
   }
   return n;
 }
