@@ -446,6 +446,20 @@ __device__ __forceinline__ uint32_t bin_or_zero(const uint32_t* N, int j, const 
   return (j >= 0 && j < C.nbins) ? N[j] : 0u;
 }
 
+// Seed record pos of S: the piece [lo, hi], its maximum bin im and the bins
+// around it (0 outside the histogram).  False if pos or im is out of range.
+__device__ __forceinline__ bool put_seed(const uint32_t* N, const Consts& C, SeedOut* S, int pos,
+                                         int lo, int hi, int im) {
+  if (!PV_CHECK(pos >= 0 && pos < kMaxSeeds && im >= 0 && im < C.nbins, 4)) return false;
+  S->lo[pos] = lo;
+  S->hi[pos] = hi;
+  S->bin[pos] = im;
+  S->nm[pos] = bin_or_zero(N, im - 1, C);
+  S->ni[pos] = N[im];
+  S->np[pos] = bin_or_zero(N, im + 1, C);
+  return true;
+}
+
 // Warp-cooperative peak search over a histogram N (shared or global).  If
 // tmask is non-null only tiles (32 bins) whose bit is set can hold non-zero
 // bins; otherwise every tile is scanned.  pc_lo / pc_hi are a kRunRing-entry
@@ -463,16 +477,9 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
   int n_starts = 0, n_ends = 0, n_done = 0;
 
   auto put = [&](int pos, int lo, int hi, int im) {
-    if (!PV_CHECK(pos >= 0 && pos < kMaxSeeds && im >= 0 && im < C.nbins, 4)) return;
-    const uint32_t nm = bin_or_zero(N, im - 1, C), ni = N[im], np = bin_or_zero(N, im + 1, C);
-    S->lo[pos] = lo;
-    S->hi[pos] = hi;
-    S->bin[pos] = im;
-    S->nm[pos] = nm;
-    S->ni[pos] = ni;
-    S->np[pos] = np;
+    if (!put_seed(N, C, S, pos, lo, hi, im)) return;
     if (kSeedZ) {
-      float zs = seed_z_from(nm, ni, np, im, C);
+      float zs = seed_z_from(S->nm[pos], S->ni[pos], S->np[pos], im, C);
       S->z[pos] = zs;
       S->x[pos] = __fadd_rn(C.x_b, __fmul_rn(C.tx_b, zs));
       S->y[pos] = __fadd_rn(C.y_b, __fmul_rn(C.ty_b, zs));

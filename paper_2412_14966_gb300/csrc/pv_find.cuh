@@ -104,6 +104,167 @@ __device__ __forceinline__ void warp_place(const CidT* cid, int n, int* base, Sl
   }
 }
 
+// Step (c) with the whole CTA, on the shared histogram N of one event (whole
+// 32-bin tiles).  Every warp scans its share of the
+// touched tiles and records, per tile, the bins where a run of bins above
+// the threshold starts and ends (smask, emask); warp 0 lists the runs in z
+// order (r_lo, r_hi: NT entries each); thread r walks run r (the proto-cluster)
+// and counts its kept pieces, keeping the first two; a
+// block-wide scan of the counts gives each piece its seed index.  Writes up to
+// cap seeds into S in z order and returns their number (which may exceed
+// cap) on every thread, or -1 on every thread when the event has more runs
+// than threads (the caller then runs the one-warp search).  misc_scan: NT/32
+// ints; misc_n: one int; mark: the recursive split's per-bin scratch.  All
+// threads of the CTA must call it.
+template <int kSplit, int NT>
+__device__ int block_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
+                                SeedOut* S, int cap, uint32_t* smask, uint32_t* emask,
+                                int16_t* r_lo, int16_t* r_hi, int* misc_scan, int* misc_n,
+                                int16_t* mark) {
+  constexpr int NW = NT / 32;
+  static_assert(kTileWords * 32 <= 4 * 32, "the run list covers at most 128 tiles");
+  static_assert(2 * kRunRing * NW >= 2 * NT, "the run list lives in the proto-cluster rings");
+  static_assert(sizeof(float4) * kFillChunk >= 2 * sizeof(uint32_t) * kTileWords * 32,
+                "the tile masks live in the fill records");
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+
+  // run starts and ends of the touched tiles, tile i of the mask to warp i mod NW
+  int rank = 0;
+#pragma unroll 1
+  for (int w = 0; w < kTileWords; ++w) {
+    uint32_t m = tmask[w];
+    while (m) {
+      const int tb = __ffs(m) - 1;
+      m &= m - 1;
+      const bool take = rank == warp;
+      rank = rank + 1 == NW ? 0 : rank + 1;
+      if (!take) continue;
+      const int q = 32 * w + tb;
+      const int bin = 32 * q + lane;
+      const bool ab = bin < C.nbins && N[bin] > C.thr;
+      const bool pa = bin >= 1 && bin - 1 < C.nbins && N[bin - 1] > C.thr;
+      const bool na = bin + 1 < C.nbins && N[bin + 1] > C.thr;
+      const unsigned st = __ballot_sync(0xffffffffu, ab && !pa);
+      const unsigned en = __ballot_sync(0xffffffffu, ab && !na);
+      if (lane == 0 && PV_CHECK(q < kTileWords * 32, 18)) {
+        smask[q] = st;
+        emask[q] = en;
+      }
+    }
+  }
+  __syncthreads();
+
+  // warp 0: the runs in z order (lane l the tiles 4l .. 4l + 3)
+  if (warp == 0) {
+    uint32_t sm[4], em[4];
+    int cs = 0, ce = 0;
+    const uint32_t tw = (lane >> 3) < kTileWords ? tmask[lane >> 3] : 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = 4 * lane + k;
+      const bool touched = ((tw >> (q & 31)) & 1u) != 0u;
+      sm[k] = touched ? smask[q] : 0u;
+      em[k] = touched ? emask[q] : 0u;
+      cs += __popc(sm[k]);
+      ce += __popc(em[k]);
+    }
+    // both counts in one scan (at most 16 runs per tile: 2048 < 2^15)
+    int inc = cs | (ce << 16);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const int tot = __shfl_sync(0xffffffffu, inc, 31);
+    const int R = tot & 0xffff;
+    if (R <= NT && (tot >> 16) == R) {
+      int ps = (inc & 0xffff) - cs, pe = (inc >> 16) - ce;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int q0 = 32 * (4 * lane + k);
+        while (sm[k]) {
+          const int b = __ffs(sm[k]) - 1;
+          sm[k] &= sm[k] - 1;
+          if (PV_CHECK(ps < NT, 19)) r_lo[ps] = static_cast<int16_t>(q0 + b);
+          ++ps;
+        }
+        while (em[k]) {
+          const int b = __ffs(em[k]) - 1;
+          em[k] &= em[k] - 1;
+          if (PV_CHECK(pe < NT, 19)) r_hi[pe] = static_cast<int16_t>(q0 + b);
+          ++pe;
+        }
+      }
+    }
+    if (lane == 0) *misc_n = ((tot >> 16) == R && R <= NT) ? R : -1;
+  }
+  __syncthreads();
+  const int R = *misc_n;
+  if (R < 0) return -1;
+
+  // thread r walks run r
+  int a = 0, b = -1;
+  uint64_t total = 0;
+  if (tid < R) {
+    a = r_lo[tid];
+    b = r_hi[tid];
+    // (a run's bounds always lie in the histogram; the test keeps a broken
+    // invariant from reading outside it)
+    if (!(a >= 0 && a <= b && b < C.nbins)) {
+      (void)PV_CHECK(false, 17);
+      b = a - 1;
+    }
+    for (int i = a; i <= b; ++i) total += N[i];
+  }
+  const uint64_t t_min = C.t_pp < C.t_gas ? C.t_pp : C.t_gas;
+  int kept = 0, lo1 = 0, hi1 = 0, im1 = 0, lo2 = 0, hi2 = 0, im2 = 0;
+  if (b >= a && total >= t_min) {
+    split_pieces<kSplit>(N, a, b, total, C,
+                         [&](int lo, int hi, uint64_t integral, int im) {
+      if (keep_piece(integral, im, C)) {
+        if (kept == 0) {
+          lo1 = lo; hi1 = hi; im1 = im;
+        } else if (kept == 1) {
+          lo2 = lo; hi2 = hi; im2 = im;
+        }
+        ++kept;
+      }
+    }, mark);
+  }
+  // each piece's index: exclusive scan of the counts in run order
+  int incl = kept;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) misc_scan[warp] = incl;
+  __syncthreads();
+  int pos = incl - kept, n_kept = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const int v = misc_scan[w];
+    if (w < warp) pos += v;
+    n_kept += v;
+  }
+  if (kept >= 1 && kept <= 2 && pos < cap) {
+    put_seed(N, C, S, pos, lo1, hi1, im1);
+    if (kept == 2 && pos + 1 < cap) put_seed(N, C, S, pos + 1, lo2, hi2, im2);
+  }
+  if (kept > 2 && pos < cap) {
+    split_pieces<kSplit>(N, a, b, total, C,
+                         [&](int lo, int hi, uint64_t integral, int im) {
+      if (keep_piece(integral, im, C)) {
+        if (pos < cap) put_seed(N, C, S, pos, lo, hi, im);
+        ++pos;
+      }
+    }, mark);
+  }
+  return n_kept;
+}
+
 // What group_fit returns for a vertex without tracks: singular at the first
 // iteration (or unconverged with no iteration when max_iter is 0).
 __device__ __forceinline__ VertexOut empty_fit(const Consts& C) {
@@ -386,14 +547,24 @@ __device__ __forceinline__ void find_event(const Consts& C, const TrackPtrs& T, 
       }
       if (tid == NT - 1 && next_slot) *next_slot = e_next;
 
-      // ---- (c): seeds from the touched tiles (warp 0)
-      if (warp == 0) {
-        const int K = warp_find_seeds<false, SPLIT>(hist, tmask, C, S, O.cap, pc_lo, pc_hi,
-                                                    reinterpret_cast<int16_t*>(smem + Lo.mark));
-        if (lane == 0) misc[kMiscK] = K;
+      // ---- (c): seeds from the touched tiles, with the whole CTA (with warp
+      // 0 alone when the event has more runs than threads)
+      int16_t* mark = reinterpret_cast<int16_t*>(smem + Lo.mark);
+      int16_t* runs = reinterpret_cast<int16_t*>(smem + Lo.ring);
+      uint32_t* tiles = reinterpret_cast<uint32_t*>(smem + Lo.uni);
+      int Kall = block_find_seeds<SPLIT, NT>(hist, tmask, C, S, O.cap, tiles,
+                                             tiles + kTileWords * 32, runs, runs + NT,
+                                             misc + kMiscWarpScan, misc + kMiscFlag, mark);
+      if (Kall < 0) {
+        if (warp == 0) {
+          const int K = warp_find_seeds<false, SPLIT>(hist, tmask, C, S, O.cap, pc_lo, pc_hi, mark);
+          if (lane == 0) misc[kMiscK] = K;
+        }
+        __syncthreads();
+        Kall = misc[kMiscK];
+      } else {
+        __syncthreads();
       }
-      __syncthreads();
-      const int Kall = misc[kMiscK];
       const int K = Kall < O.cap ? Kall : O.cap;
       // clear the touched tiles for the next event (warp w the tiles of mask
       // word w, w + NW, ...)
