@@ -308,6 +308,36 @@ static __device__ __noinline__ void write_empty_vertex(const Consts& C, const Ou
   write_vertex(C, O, e, k, S->x[k], S->y[k], S->z[k], empty_fit(C));
 }
 
+// Serving: the vertices a CTA has found and not yet fitted, from up to
+// kServeReqs requests.  The serving kernel fits them kServeFitBatch at a time
+// (four 8-lane groups in each of its four warps), so it lets them gather
+// before a round while more published events wait.
+constexpr int kServeFitBatch = 16;
+// a round starts once this many are queued (so that most rounds, with the
+// vertices of the event that crossed it, still take one pass)
+constexpr int kServeRoundAt = 12;
+constexpr int kServeQueue = kServeRoundAt - 1 + kMaxSeeds;   // most vertices queued
+constexpr int kServeReqs = 4;
+struct ServeReq {                    // a request with queued events
+  OutPtrs O;
+  float4* A;
+  float2* W;
+  unsigned long long slot, target, seq;
+  int events;                        // its events found since the last round
+};
+struct ServeVertex {                 // one vertex to fit (cnt > 0 tracks)
+  int off;                           // fit inputs A[off ..], W[off ..] of its request
+  int cnt, e, k, req;
+  float x, y, z;                     // seed position
+};
+struct ServeQueue {
+  int n;                             // vertices queued
+  int nreq;                          // requests with events since the last round
+  int16_t order[kServeQueue];
+  ServeVertex v[kServeQueue];
+  ServeReq req[kServeReqs];
+};
+
 __device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tracks) {
   return b0 < 0 || b1 < b0 || b1 > n_tracks || b1 - b0 > 0x7fffffffLL;
 }
@@ -360,14 +390,14 @@ __device__ __forceinline__ void find_prologue(const Consts& C, unsigned char* sm
 // The find kernel's work on one event e (all threads of the CTA; smem is the
 // dynamic shared memory laid out by make_layout).  next_slot / e_next: the
 // event claimed for the next iteration, published in shared memory after the
-// fill (NULL when the caller claims otherwise).  With kServe in MODE the CTA
-// also fits the event's vertices (binary32 sums per kAccum) instead of
-// listing them for the fit kernel.
-template <int MODE, int NT, int FLAV, int kAccum = PV_ACCUM_FP32>
+// fill (NULL when the caller claims otherwise).  With kServe in MODE the
+// event's vertices join the CTA's queue Q (request Q->nreq - 1) instead of the
+// fit kernel's work lists.
+template <int MODE, int NT, int FLAV>
 __device__ __forceinline__ void find_event(const Consts& C, const TrackPtrs& T, const SeedPtrs& SP,
                                            const OutPtrs& O, const TrackScratch& G,
                                            unsigned char* smem, int e, int* next_slot,
-                                           int e_next) {
+                                           int e_next, ServeQueue* Q = nullptr) {
   constexpr int SPLIT = flavour_split(FLAV);
   constexpr int PROFILE = flavour_profile(FLAV);
   constexpr int NW = NT / 32;
@@ -745,23 +775,25 @@ __device__ __forceinline__ void find_event(const Consts& C, const TrackPtrs& T, 
         fit_input(t, c, sl);
       }
       if constexpr ((MODE & kServe) != 0) {
-        // serving: the CTA fits its event's vertices, one per 8-lane group,
-        // from the fit inputs just written (a vertex without tracks gets the
-        // singular result of an empty fit)
-        __syncthreads();
-        // (vertex k goes to warp k mod NW, so that few vertices spread over
-        // all warps)
-        const int r = lane & (kGroup - 1);
-        for (int vb = 0; vb < Ka; vb += NW * kGroupsPerWarp) {
-          const int k = vb + (lane >> 3) * NW + warp;
-          const bool has = k < Ka;
-          const int cntk = has ? cnt[k] : -1;
-          const int o = has ? b0 + voff[k] : 0;
-          VertexOut v;
-          group_fit<kAccum>(G.A + o + r, G.W + o + r, kGroup, cntk, C, &v);
-          if (has && r == 0) {
-            if (cntk > 0) write_vertex(C, O, e, k, S->x[k], S->y[k], S->z[k], v);
-            else write_empty_vertex(C, O, S, e, k);
+        // serving: the vertices with tracks join the CTA's queue, a vertex
+        // without tracks gets the singular result of an empty fit now
+        if (tid < Ka) {
+          const int c = cnt[tid];
+          if (c > 0) {
+            const int qi = atomicAdd(&Q->n, 1);
+            if (PV_CHECK(qi < kServeQueue, 20)) {
+              ServeVertex& v = Q->v[qi];
+              v.off = static_cast<int>(b0 + voff[tid]);
+              v.cnt = c;
+              v.e = e;
+              v.k = tid;
+              v.req = Q->nreq - 1;
+              v.x = S->x[tid];
+              v.y = S->y[tid];
+              v.z = S->z[tid];
+            }
+          } else {
+            write_empty_vertex(C, O, S, e, tid);
           }
         }
       }

@@ -2,9 +2,11 @@
 // requests on the device.
 //
 // Each CTA loops: it claims the next event of the published request
-// sequence (ServeCtl / ServeDev in pv_kernels.cuh), runs steps (a)-(d3) on it
-// -- the batched find kernel's event work, with the event's vertices fitted in
-// the same CTA -- and, if the event was its request's last to finish, stamps
+// sequence (ServeCtl / ServeDev in pv_kernels.cuh) and runs steps (a)-(d1) on
+// it -- the batched find kernel's event work -- queueing the event's vertices;
+// the CTA fits its queue (d2, d3) in rounds of 16 vertices, from whichever
+// requests they came, whenever a round's worth has gathered or it would
+// otherwise wait, and the round that finishes a request's last events stamps
 // the request's completion with the GPU's global timer.  Requests that arrive
 // while others run are picked up as CTAs free up, so their events overlap on
 // the device; a request's results do not depend on what ran beside it.  Every
@@ -80,9 +82,73 @@ __device__ __forceinline__ bool read_desc(const ServeDesc* d, ServeDesc* s,
   return __shfl_sync(0xffffffffu, s2, 0) == seq;
 }
 
-// 64 registers per thread, eight CTAs per SM (measured on the nominal batch as
-// one request: 14.5 M events/s at four CTAs per SM, 17.9 M at six, 19.0 M at
-// eight)
+// One fitting round of the CTA's queue (all threads): the queued vertices by
+// track count, largest first, four to a warp (so that a warp's groups need
+// similar numbers of passes), each fitted by an 8-lane group with binary32
+// sums per kAccum; then each request with events in the round counts them
+// done, and the round that completes a request stamps its completion with the
+// global timer.  The queue is empty afterwards.
+template <int kAccum>
+__device__ __forceinline__ void serve_round(const Consts& C, ServeQueue& Q, ServeCtl* ctl,
+                                            ServeDev* dev) {
+  constexpr int NW = kServeThreads / 32;
+  static_assert(NW * kGroupsPerWarp == kServeFitBatch, "a round fills every group");
+  static_assert(kServeQueue <= kServeThreads, "one thread per queued vertex ranks them");
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int n = Q.n < kServeQueue ? Q.n : kServeQueue;
+  if (tid < n) {
+    const int ck = Q.v[tid].cnt;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const int cj = Q.v[j].cnt;
+      rank += (cj > ck || (cj == ck && j < tid)) ? 1 : 0;
+    }
+    Q.order[rank] = static_cast<int16_t>(tid);
+  }
+  __syncthreads();
+  const int r = lane & (kGroup - 1);
+  for (int vb = 0; vb < n; vb += kServeFitBatch) {
+    const int sl = vb + warp * kGroupsPerWarp + (lane >> 3);
+    const bool has = sl < n;
+    const ServeVertex v = Q.v[has ? Q.order[sl] : Q.order[vb]];
+    const int q = (v.req >= 0 && v.req < kServeReqs) ? v.req : 0;
+    (void)PV_CHECK(v.req == q, 21);
+    const ServeReq& R = Q.req[q];
+    VertexOut out;
+    group_fit<kAccum>(R.A + v.off + r, R.W + v.off + r, kGroup, has ? v.cnt : -1, C, &out);
+    if (has && r == 0) write_vertex(C, R.O, v.e, v.k, v.x, v.y, v.z, out);
+  }
+  // the round's outputs are visible device-wide before its events count as done
+  __threadfence();
+  __syncthreads();
+  if (tid < Q.nreq && tid < kServeReqs) {
+    const ServeReq& R = Q.req[tid];
+    if (R.events > 0) {
+      const unsigned long long ev = static_cast<unsigned long long>(R.events);
+      const unsigned long long before = atomicAdd(&dev->slot_done[R.slot], ev);
+      if (before + ev == R.target) {
+        // the request's last events: its outputs are complete
+        __threadfence_system();
+        *reinterpret_cast<volatile unsigned long long*>(&ctl->done_ns[R.slot]) = global_ns();
+        st_release_sys(&ctl->done_seq[R.slot], R.seq);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    Q.n = 0;
+    Q.nreq = 0;
+  }
+  __syncthreads();
+}
+
+// 64 registers per thread, eight CTAs per SM, which is also what shared memory
+// allows (the find's histogram and tables plus the queue: about 25 KB per
+// CTA).  Measured on the nominal batch as one request, with the vertices then
+// fitted per event: 14.5 M events/s at four CTAs per SM, 17.9 M at six, 19.0 M
+// at eight.
 template <int FLAV, int kAccum>
 __global__ void __launch_bounds__(kServeThreads, 8)
 serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
@@ -92,35 +158,67 @@ serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
   const Layout Lo = make_layout(C.nbins, kFindFit, NT, flavour_split(FLAV) == PV_SPLIT_RECURSIVE);
   find_prologue<kFindFit, NT>(C, smem, Lo);
   __shared__ ServeDesc s_d;
+  __shared__ ServeQueue Q;
   __shared__ unsigned long long s_g;
-  __shared__ int s_code;
+  __shared__ int s_code, s_round;
   // warp 0's state: the request the last event fell in, the published count
-  // seen last
-  unsigned long long cursor = seq_start, pub = 0;
+  // seen last; lane 0's: the event claimed ahead
+  unsigned long long cursor = seq_start, pub = 0, ahead = 0;
   bool orphans_left = true;           // lane 0: the previous launch's list not exhausted
-  bool have = false;
+  bool have = false, have_ahead = false;
   const int prev = (epoch + 1) & 1, cur = epoch & 1;
+  if (threadIdx.x == 0) {
+    Q.n = 0;
+    Q.nreq = 0;
+  }
   __syncthreads();
   for (;;) {
-    if (threadIdx.x < 32) {
-      // the next event (lane 0): first the events the previous launch handed
-      // on, then the next of the sequence; it is processed once published
-      // (bounded wait; an event still unpublished when the wait ends, or when
-      // the host asks to stop, is handed on to the next launch)
-      int code = -1;
+    if (threadIdx.x == 0) {
+      // the next event: first the events the previous launch handed on, then
+      // the one claimed ahead, else a new claim
+      bool got = false;
       unsigned long long g = 0;
-      if (threadIdx.x == 0) {
-        bool got = false;
-        if (orphans_left) {
-          const int i = atomicAdd(&dev->orph_take, 1);
-          if (i < dev->orph_n[prev] && i < kServeOrphans) {
-            g = dev->orph[prev][i];
-            got = true;
-          } else {
-            orphans_left = false;
-          }
+      if (orphans_left) {
+        const int i = atomicAdd(&dev->orph_take, 1);
+        if (i < dev->orph_n[prev] && i < kServeOrphans) {
+          g = dev->orph[prev][i];
+          got = true;
+        } else {
+          orphans_left = false;
         }
-        if (!got) g = atomicAdd(&dev->next_event, 1ull);
+      }
+      if (!got) {
+        if (have_ahead) {
+          g = ahead;
+          have_ahead = false;
+        } else {
+          g = atomicAdd(&dev->next_event, 1ull);
+        }
+      }
+      if (g >= pub) pub = ld_acquire_sys(&ctl->published);
+      // with plenty of published events left, claim the one after now (its
+      // atomic completes while this event runs)
+      if (!orphans_left && g + gridDim.x < pub) {
+        ahead = atomicAdd(&dev->next_event, 1ull);
+        have_ahead = true;
+      }
+      // fit the queue first when it holds kServeRoundAt vertices, when
+      // the event is not published yet (the CTA may wait), or when the event
+      // may need a request entry and none is free
+      const bool same = have && g >= s_d.ev_base &&
+                        g < s_d.ev_base + static_cast<unsigned long long>(s_d.T.n_events);
+      s_round = Q.nreq > 0 && (Q.n >= kServeRoundAt || g >= pub || (!same && Q.nreq >= kServeReqs));
+      s_g = g;
+    }
+    __syncthreads();
+    if (s_round) serve_round<kAccum>(C, Q, ctl, dev);
+    if (threadIdx.x < 32) {
+      // the event is processed once published (bounded wait; an event still
+      // unpublished when the wait ends, or when the host asks to stop, is
+      // handed on to the next launch with the one claimed ahead)
+      const unsigned long long g = s_g;
+      int code = -1;
+      if (threadIdx.x == 0) {
         const unsigned long long t0 = global_ns();
         unsigned int nap = 32;
         while (g >= pub) {
@@ -128,8 +226,13 @@ serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
           if (g < pub) break;
           const bool stop = ld_acquire_sys(&ctl->stop) != 0u;
           if (stop || global_ns() - t0 > idle_ns) {
-            const int i = atomicAdd(&dev->orph_n[cur], 1);
+            int i = atomicAdd(&dev->orph_n[cur], 1);
             if (i < kServeOrphans) dev->orph[cur][i] = g;
+            if (have_ahead) {
+              i = atomicAdd(&dev->orph_n[cur], 1);
+              if (i < kServeOrphans) dev->orph[cur][i] = ahead;
+              have_ahead = false;
+            }
             code = stop ? PV_OK : PV_ERR_TIMEOUT;
             break;
           }
@@ -146,7 +249,6 @@ serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
         }
       }
       code = __shfl_sync(0xffffffffu, code, 0);
-      g = __shfl_sync(0xffffffffu, g, 0);
       // (events handed on by the previous launch come in any order: one
       // before the request last found restarts the search at the oldest
       // request of this launch)
@@ -174,8 +276,20 @@ serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
         __syncwarp();
       }
       if (threadIdx.x == 0) {
-        s_g = g;
         s_code = code;
+        // the event's request: a queue entry (a new one unless the last is it)
+        if (code < 0 && (Q.nreq == 0 || Q.req[Q.nreq - 1].seq != s_d.seq) &&
+            PV_CHECK(Q.nreq < kServeReqs, 22)) {
+          ServeReq& R = Q.req[Q.nreq];
+          R.O = s_d.O;
+          R.A = s_d.A;
+          R.W = s_d.W;
+          R.slot = s_d.seq % kServeRing;
+          R.target = s_d.done_target;
+          R.seq = s_d.seq;
+          R.events = 0;
+          ++Q.nreq;
+        }
       }
     }
     __syncthreads();
@@ -189,23 +303,13 @@ serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
     G.slot = s_d.slot;
     G.A = s_d.A;
     G.W = s_d.W;
-    const unsigned long long slot = s_d.seq % kServeRing, target = s_d.done_target,
-                             seq = s_d.seq;
     __syncthreads();                 // s_d may change once thread 0 claims again
-    find_event<kFindFit | kServe, NT, FLAV, kAccum>(C, T, SeedPtrs{}, O, G, smem, e, nullptr, 0);
-    // the event's outputs are visible device-wide before it counts as done
-    __threadfence();
+    find_event<kFindFit | kServe, NT, FLAV>(C, T, SeedPtrs{}, O, G, smem, e, nullptr, 0, &Q);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned long long before = atomicAdd(&dev->slot_done[slot], 1ull);
-      if (before + 1 == target) {
-        // the request's last event: its outputs are complete
-        __threadfence_system();
-        *reinterpret_cast<volatile unsigned long long*>(&ctl->done_ns[slot]) = global_ns();
-        st_release_sys(&ctl->done_seq[slot], seq);
-      }
-    }
+    if (threadIdx.x == 0) Q.req[Q.nreq - 1].events += 1;
   }
+  // the vertices still queued
+  if (Q.nreq > 0) serve_round<kAccum>(C, Q, ctl, dev);
   if (threadIdx.x == 0) {
     if (atomicAdd(&dev->running, 1) + 1 == static_cast<int>(gridDim.x)) {
       // the last CTA to leave records why
