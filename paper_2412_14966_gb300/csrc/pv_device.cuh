@@ -728,6 +728,12 @@ __device__ __forceinline__ double group_sum(double v) {
   v += __shfl_xor_sync(0xffffffffu, v, 1);
   return v;
 }
+__device__ __forceinline__ float group_max(float v) {
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+  return v;
+}
 __device__ __forceinline__ int group_sum_i(int v) {
   v += __shfl_xor_sync(0xffffffffu, v, 4);
   v += __shfl_xor_sync(0xffffffffu, v, 2);

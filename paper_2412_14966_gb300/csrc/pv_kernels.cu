@@ -217,22 +217,54 @@ __device__ __forceinline__ float mv_chi2_at(const MvTrack& m, const MvLast& L) {
   return rx * rx * m.wx + ry * ry * m.wy;
 }
 
-// Multi-vertex fit of one vertex per 8-lane group (binary32 sums), over all n
-// tracks of the event whose packed records start at rec (lane r of the group
-// takes every 8th).  Same normal equations, shear and solve as group_fit; the
-// stop rule is |dz| < mv_dz_tol alone and a track counts for the vertex from
-// weight mv_w_assoc on.  Every lane of the warp must call it.
-__device__ void group_fit_multi(const float4* rec, int n, float xs, float ys, float zs,
-                                bool active, const Consts& C, VertexOut* out, MvLast* last) {
-  const int r = threadIdx.x & (kGroup - 1);
+// The window of the multi-vertex fit: a vertex's fit visits the tracks with
+// chi2 < kMvWin at its seed; the others must keep chi2 >= kMvSafe at every
+// iterate (so each weighs under exp(2 - kMvSafe/2) ~ 7e-13 of a track at the
+// vertex, below binary32 resolution of the sums), else the vertex is fitted
+// over all tracks.
+constexpr float kMvWin = 200.0f;
+constexpr float kMvSafe = 60.0f;
+constexpr int kMvList = 128;           // most tracks a vertex's window holds
+
+// Multi-vertex fit of one vertex per G-lane group (binary32 sums), over the
+// tracks of the event whose packed records start at rec: all n of them (list
+// NULL) or the n listed (list[j] = track index); lane r of the group takes
+// every G-th.  Same normal equations, shear and solve as group_fit; the stop
+// rule is |dz| < mv_dz_tol alone and a track counts for the vertex from
+// weight mv_w_assoc on.  With a list, the fit stops with *escaped set when an
+// iterate a (relative to the seed) moves far enough that a track left out
+// could come within chi2 kMvSafe: a track's residual changes by
+// (a_z t_x - a_x, a_z t_y - a_y), so by Minkowski's inequality its sqrt(chi2)
+// drops by at most sqrt(w_max) (|a_x| + |a_y| + 2 |a_z| t_max) (w_max its larger
+// weight 1/V, t_max its larger |slope|), which stays below its margin
+// m = sqrt(chi2 at the seed) - sqrt(kMvSafe) while
+// (|a_x| + |a_y|) i_xy + 2 |a_z| i_z <= 1, i_xy and i_z being the largest
+// sqrt(w_max)/m and sqrt(w_max) t_max/m over the tracks left out.  Every lane
+// of the warp must call it.
+// Sum over the G lanes of a group (G = 8 or 32; xor tree, identical on all its
+// lanes).  Every lane of the warp must call it.
+template <int G, typename T>
+__device__ __forceinline__ T lanes_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int G>
+__device__ void group_fit_multi(const float4* rec, int n, const int16_t* list, float xs,
+                                float ys, float zs, bool active, const Consts& C, VertexOut* out,
+                                MvLast* last, float i_xy = 0.f, float i_z = 0.f,
+                                bool* escaped = nullptr) {
+  const int r = threadIdx.x & (G - 1);
   const int cnt = active ? n : 0;
   float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-  for (int s = r; s < cnt; s += kGroup) {
+  for (int s = r; s < cnt; s += G) {
     MvTrack m;
-    if (!mv_track(rec + 3 * s, xs, ys, zs, &m)) continue;
+    const int t = list ? static_cast<int>(list[s]) : s;
+    if (!mv_track(rec + 3 * t, xs, ys, zs, &m)) continue;
     m0 += m.wx; m1 += m.wx * m.tx; m2 += m.wy; m3 += m.wy * m.ty;
   }
-  m0 = group_sum(m0); m1 = group_sum(m1); m2 = group_sum(m2); m3 = group_sum(m3);
+  m0 = lanes_sum<G>(m0); m1 = lanes_sum<G>(m1); m2 = lanes_sum<G>(m2); m3 = lanes_sum<G>(m3);
   float cx = m0 > 0.f ? m1 / m0 : 0.f;
   float cy = m2 > 0.f ? m3 / m2 : 0.f;
   float ax = 0.f, ay = 0.f, az = 0.f;
@@ -247,10 +279,20 @@ __device__ void group_fit_multi(const float4* rec, int n, float xs, float ys, fl
     for (int q = 0; q < 10; ++q) v[q] = 0.f;
     int cnt_w = 0;
     const MvLast P{ax - cx * az, ay - cy * az, az, cx, cy};
+    if (!done && list) {
+      // the tracks left out stay out of reach of this iterate?
+      const float axy = (ax < 0.f ? -ax : ax) + (ay < 0.f ? -ay : ay);
+      const float az_ = az < 0.f ? -az : az;
+      if (!(axy * i_xy + 2.0f * az_ * i_z <= 1.0f)) {
+        *escaped = true;
+        done = true;
+      }
+    }
     if (!done) {
-      for (int s = r; s < cnt; s += kGroup) {
+      for (int s = r; s < cnt; s += G) {
         MvTrack m;
-        if (!mv_track(rec + 3 * s, xs, ys, zs, &m)) continue;
+        const int t = list ? static_cast<int>(list[s]) : s;
+        if (!mv_track(rec + 3 * t, xs, ys, zs, &m)) continue;
         const float dtx = m.tx - P.cx, dty = m.ty - P.cy;
         const float rx = m.X + P.az * dtx - P.axp;
         const float ry = m.Y + P.az * dty - P.ayp;
@@ -267,8 +309,8 @@ __device__ void group_fit_multi(const float4* rec, int n, float xs, float ys, fl
       }
     }
 #pragma unroll
-    for (int q = 0; q < 10; ++q) v[q] = group_sum(v[q]);
-    cnt_w = group_sum_i(cnt_w);
+    for (int q = 0; q < 10; ++q) v[q] = lanes_sum<G>(v[q]);
+    cnt_w = lanes_sum<G>(cnt_w);
     if (!done) {
       const float sxx = v[0], syy = v[1], sxz = v[2], syz = v[3], szz = v[4];
       const float bx = v[5], by = v[6], bz = v[7];
@@ -416,33 +458,88 @@ mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
     if (PV_CHECK(K <= kMaxSeeds, 13)) M.work[wb + k] = make_int2(e, k);
 }
 
-// Multi-vertex fits from the work list: every 8-lane group fits one vertex,
-// its lanes visiting every track of the event.  The fits wait on their track
-// loads, so four CTAs per SM (64 registers, a few spilled) beat two (97
-// registers): 1.30 ms against 1.56 ms per nominal step.
+// Multi-vertex fits from the work list: every 8-lane group fits one vertex.
+// kRedo = false: over the vertex's window (the tracks with chi2 < kMvWin at
+// its seed, listed in shared memory in track order); a vertex whose window
+// does not hold -- more than kMvList tracks or none, a track left out came
+// within reach, the fit was singular, or the listed tracks' weights sum below
+// one half (ndof = 2 sum w - 3), where tracks left out would no longer be
+// negligible -- goes to the refit list instead of the outputs.  kRedo = true:
+// the refit list, each vertex over every track of its event.  The fits wait on
+// their track loads, so four CTAs per SM (64 registers, a few spilled) beat
+// two (97 registers): 1.30 ms against 1.56 ms per nominal step.
+template <bool kRedo>
 __global__ void __launch_bounds__(kMvFitThreads, 4)
 mv_fit_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
+  __shared__ int16_t s_list[kRedo ? 1 : kMvFitThreads / kGroup][kRedo ? 1 : kMvList];
   const int lane = threadIdx.x & 31;
   const int r = lane & (kGroup - 1);
-  const int n_items = M.counters[0];
+  const int n_items = kRedo ? M.counters[2] : M.counters[0];
+  int* next = M.counters + (kRedo ? 3 : 1);
   for (;;) {
     int b = 0;
-    if (lane == 0) b = atomicAdd(M.counters + 1, kGroupsPerWarp);
+    if (lane == 0) b = atomicAdd(next, kGroupsPerWarp);
     b = __shfl_sync(0xffffffffu, b, 0);
     if (b >= n_items) break;
     const int v = b + (lane >> 3);
     const bool has = v < n_items;
-    const int2 it = has ? M.work[v] : make_int2(0, 0);
+    const int2 it = !has ? make_int2(0, 0) : (kRedo ? M.redo[v] : M.work[v]);
     const int e = it.x, k = it.y;
     const int64_t b0 = has ? T.off[e] : 0;
     const int n = has ? static_cast<int>(T.off[e + 1] - b0) : 0;
     const size_t slot = static_cast<size_t>(e) * kMaxSeeds + k;
     const float xs = has ? M.sx[slot] : 0.f, ys = has ? M.sy[slot] : 0.f;
     const float zs = has ? M.sz[slot] : 0.f;
+    const float4* rec = M.P + 3 * b0;
     VertexOut out;
     MvLast L;
-    group_fit_multi(M.P + 3 * b0, n, xs, ys, zs, has, C, &out, &L);
-    if (has && r == 0) {
+    bool keep = has;
+    if constexpr (kRedo) {
+      group_fit_multi<kGroup>(rec, n, nullptr, xs, ys, zs, has, C, &out, &L);
+    } else {
+      // the window, and the bound on the tracks left out (i_xy, i_z)
+      int16_t* list = s_list[threadIdx.x >> 3];
+      const unsigned gmask = 0xffu << (lane & 24);
+      int nn = 0;
+      float ixy = 0.f, iz = 0.f;
+      for (int j0 = 0; j0 < n; j0 += kGroup) {     // (n is the same on the group's lanes)
+        const int sidx = j0 + r;
+        bool near = false;
+        if (sidx < n) {
+          MvTrack m;
+          if (mv_track(rec + 3 * sidx, xs, ys, zs, &m)) {
+            const float c2 = m.X * m.X * m.wx + m.Y * m.Y * m.wy;
+            if (c2 < kMvWin) {
+              near = true;
+            } else {
+              const float rm = 1.0f / (sqrtf(c2) - sqrtf(kMvSafe));
+              const float sw = sqrtf(fmaxf(m.wx, m.wy));
+              ixy = fmaxf(ixy, sw * rm);
+              iz = fmaxf(iz, sw * fmaxf(fabsf(m.tx), fabsf(m.ty)) * rm);
+            }
+          }
+        }
+        const unsigned bal = (__ballot_sync(gmask, near) >> (lane & 24)) & 0xffu;
+        const int idx = nn + __popc(bal & ((1u << r) - 1u));
+        if (near && idx < kMvList) list[idx] = static_cast<int16_t>(sidx);
+        nn += __popc(bal);
+      }
+      ixy = group_max(ixy);
+      iz = group_max(iz);
+      __syncwarp();
+      const bool windowed = has && nn >= 1 && nn <= kMvList && n <= 32767;   // (int16 indices)
+      bool escaped = false;
+      group_fit_multi<kGroup>(rec, windowed ? nn : 0, windowed ? list : nullptr, xs, ys, zs,
+                              windowed, C, &out, &L, ixy, iz, &escaped);
+      const bool redo = has && (!windowed || escaped || (out.status & PV_ST_SINGULAR) != 0 ||
+                                !(out.ndof >= -2.0f));
+      if (redo && r == 0) {
+        const int q = atomicAdd(M.counters + 2, 1);
+        M.redo[q] = it;
+      }
+      keep = has && !redo;
+    }
+    if (keep && r == 0) {
       const size_t q = static_cast<size_t>(e) * O.cap + k;
       O.x[q] = xs + out.x;
       O.y[q] = ys + out.y;
@@ -524,20 +621,21 @@ mv_final_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
 cudaError_t launch_mv_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
                           const OutPtrs& O, const MvScratch& M, int fit_grid, cudaStream_t st,
                           int* n_launches) {
-  cudaError_t err = cudaMemsetAsync(M.counters, 0, 2 * sizeof(int), st);
+  cudaError_t err = cudaMemsetAsync(M.counters, 0, 4 * sizeof(int), st);
   if (err != cudaSuccess) return err;
   const int per_block = kMvThreads / 32;
   const int grid = (T.n_events + per_block - 1) / per_block;
   mv_seed_kernel<<<grid, kMvThreads, 0, st>>>(C, T, S, O, M);
-  mv_fit_kernel<<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
+  mv_fit_kernel<false><<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
+  mv_fit_kernel<true><<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
   mv_final_kernel<<<grid, kMvThreads, 0, st>>>(C, T, O, M);
-  *n_launches += 3;
+  *n_launches += 4;
   return cudaGetLastError();
 }
 
 int mv_blocks_per_sm(void) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mv_fit_kernel, kMvFitThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mv_fit_kernel<false>, kMvFitThreads, 0) !=
       cudaSuccess)
     return 0;
   return blocks;

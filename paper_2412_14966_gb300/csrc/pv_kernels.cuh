@@ -243,11 +243,13 @@ struct MvLastState {        // the sheared position a vertex's last weights were
   float axp, ayp, az, cx, cy;
 };
 struct MvScratch {
-  int* counters;            // [0] work items listed, [1] next item to fit
+  int* counters;            // [0] work items listed, [1] next item to fit, [2] vertices
+                            // listed for a refit over all tracks, [3] next one to refit
   int* K;                   // per event: seeds fitted
   float4* P;                // per track, three float4: x y z tx | ty cxx cxtx ctxtx |
                             // cyy cyty ctyty S, S = sum over the event's seeds of exp(-chi2/2)
   int2* work;               // (event, seed) per vertex
+  int2* redo;               // (event, seed) per vertex to refit over all tracks
   float *sx, *sy, *sz;      // per slot [event][kMaxSeeds]: seed position
   MvLastState* last;        // per slot: last-iteration state
   float *vz, *vczz;         // per slot: fitted z and C_zz
