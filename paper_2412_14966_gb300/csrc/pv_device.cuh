@@ -337,10 +337,9 @@ __host__ __device__ void split_walk(const uint32_t* N, int a, int b, uint64_t to
 // its argmax (lowest index).  Pieces come out in z order, so every piece but
 // the last ends at the split point of the innermost pending right-hand side,
 // which starts one bin later: the pending sides need no stack, only their last
-// bin, kept in mark[] at their split point (mark: one int16 per histogram bin,
-// scratch; the proto-clusters of different lanes are disjoint).  A left side's
-// integral is summed while it is split off, a right side's during its maxima
-// scan.
+// bin, kept in mark[m - a] at their split point m (mark: b - a + 1 int16
+// entries of scratch).  A left side's integral is summed while it is split
+// off, a right side's during its maxima scan.
 template <class Emit>
 __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64_t total,
                                          const Consts& C, Emit&& emit, int16_t* mark) {
@@ -393,7 +392,7 @@ __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64
         for (int i = lo; i <= m; ++i) left += N[i];
         const uint64_t right = integral - left;
         if (left >= T && right >= T) {
-          mark[m] = static_cast<int16_t>(hi);   // the pending side [m + 1, hi]
+          mark[m - a] = static_cast<int16_t>(hi);   // the pending side [m + 1, hi]
           hi = m;
           integral = left;
           known = true;
@@ -404,19 +403,94 @@ __host__ __device__ void split_recursive(const uint32_t* N, int a, int b, uint64
     emit(lo, hi, integral, m1);
     if (hi >= b) break;
     lo = hi + 1;
-    hi = mark[hi];
+    hi = mark[hi - a];
     known = false;
   }
 }
 
-// The pieces of proto-cluster [a, b] in the chosen flavour (mark: the
-// recursive split's per-bin scratch, unused by the z-order walk).
+// The same pieces as split_recursive without scratch: each piece is found by
+// descending the splitting tree from [a, b] towards the first bin not yet
+// emitted (every decision depends only on the range and its integral, so the
+// descent meets the same ranges; a right side's integral is the parent's minus
+// its left side's).  Each piece costs the scans of its ancestors: for
+// proto-clusters longer than the scratch the caller can give.
+template <class Emit>
+__host__ __device__ void split_recursive_descend(const uint32_t* N, int a, int b, uint64_t total,
+                                                 const Consts& C, Emit&& emit) {
+  for (int start = a; start <= b;) {
+    int lo = a, hi = b;
+    uint64_t integral = total;
+    for (;;) {
+      int m1 = -1, m2 = -1;
+      uint32_t v1 = 0, v2 = 0;
+      {
+        int run = lo;
+        uint32_t v = N[lo];
+        bool left_lower = true;
+        for (int i = lo + 1; i <= hi + 1; ++i) {
+          const uint32_t nv = i <= hi ? N[i] : 0u;
+          if (i > hi || nv != v) {
+            if (left_lower && (i > hi || nv < v)) {
+              if (m1 < 0 || v > v1) {
+                m2 = m1; v2 = v1;
+                m1 = run; v1 = v;
+              } else if (m2 < 0 || v > v2) {
+                m2 = run; v2 = v;
+              }
+            }
+            left_lower = v < nv;
+            run = i;
+            v = nv;
+          }
+        }
+      }
+      int m = -1;
+      uint64_t left = 0;
+      bool split = false;
+      if (m2 >= 0) {
+        const int l = m1 < m2 ? m1 : m2, h = m1 < m2 ? m2 : m1;
+        uint32_t vm = 0;
+        for (int i = l + 1; i < h; ++i) {
+          const uint32_t x = N[i];
+          if (m < 0 || x < vm) { m = i; vm = x; }
+        }
+        const uint32_t lower = v1 < v2 ? v1 : v2;
+        if (m >= 0 &&
+            static_cast<uint64_t>(C.dip_den) * vm < static_cast<uint64_t>(C.dip_num) * lower) {
+          const uint64_t T = (m < C.gas_bin) ? C.t_gas : C.t_pp;
+          for (int i = lo; i <= m; ++i) left += N[i];
+          split = left >= T && integral - left >= T;
+        }
+      }
+      if (!split) {
+        emit(lo, hi, integral, m1);
+        start = hi + 1;
+        break;
+      }
+      if (start <= m) {
+        hi = m;
+        integral = left;
+      } else {
+        lo = m + 1;
+        integral -= left;
+      }
+    }
+  }
+}
+
+// The pieces of proto-cluster [a, b] in the chosen flavour (mark: b - a + 1
+// entries of scratch for the recursive split, which runs without it when
+// mark is NULL; unused by the z-order walk).
 template <int kSplit, class Emit>
 __host__ __device__ __forceinline__ void split_pieces(const uint32_t* N, int a, int b,
                                                       uint64_t total, const Consts& C,
                                                       Emit&& emit, int16_t* mark) {
-  if constexpr (kSplit == PV_SPLIT_RECURSIVE) split_recursive(N, a, b, total, C, emit, mark);
-  else split_walk(N, a, b, total, C, emit);
+  if constexpr (kSplit == PV_SPLIT_RECURSIVE) {
+    if (mark) split_recursive(N, a, b, total, C, emit, mark);
+    else split_recursive_descend(N, a, b, total, C, emit);
+  } else {
+    split_walk(N, a, b, total, C, emit);
+  }
 }
 
 // A piece is a seed cluster if it holds the minimal integral of the region of
@@ -463,14 +537,15 @@ __device__ __forceinline__ bool put_seed(const uint32_t* N, const Consts& C, See
 // Warp-cooperative peak search over a histogram N (shared or global).  If
 // tmask is non-null only tiles (32 bins) whose bit is set can hold non-zero
 // bins; otherwise every tile is scanned.  pc_lo / pc_hi are a kRunRing-entry
-// ring in shared memory; mark (the recursive split's scratch, one int16 per
-// bin) is needed by that flavour only.  Writes up to cap seeds into S in z
-// order and returns the number found (which may exceed cap).  All 32 lanes
-// must call it.
+// ring in shared memory; mark (mark_cap int16 entries) is the recursive
+// split's scratch, shared out among the proto-clusters walked at once (one
+// whose share does not fit splits without scratch).  Writes up to cap seeds
+// into S in z order and returns the number found (which may exceed cap).
+// All 32 lanes must call it.
 template <bool kSeedZ, int kSplit = PV_SPLIT_ZORDER>
-__device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
+__device__ __noinline__ int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
                                       SeedOut* S, int cap, int16_t* pc_lo, int16_t* pc_hi,
-                                      int16_t* mark = nullptr) {
+                                      int16_t* mark = nullptr, int mark_cap = 0) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int n_seeds = 0;
@@ -505,6 +580,17 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
     // one below the smaller threshold yields no seed: skip its walk
     const uint64_t t_min = C.t_pp < C.t_gas ? C.t_pp : C.t_gas;
     const bool walk = lane < count && total >= t_min;
+    // each walked proto-cluster's share of the scratch (recursive split)
+    int16_t* lane_mark = nullptr;
+    if constexpr (kSplit == PV_SPLIT_RECURSIVE) {
+      const int len = walk ? b - a + 1 : 0;
+      int end = len;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, end, o);
+        if (lane >= o) end += v;
+      }
+      if (walk && mark && end <= mark_cap) lane_mark = mark + (end - len);
+    }
     int kept = 0, lo1 = 0, hi1 = 0, im1 = 0;
     int lo2 = 0, hi2 = 0, im2 = 0;
     if (walk) {
@@ -517,7 +603,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
           }
           ++kept;
         }
-      }, mark);
+      }, lane_mark);
     }
     int incl = kept;
     for (int o = 1; o < 32; o <<= 1) {
@@ -536,7 +622,7 @@ __device__ inline int warp_find_seeds(const uint32_t* N, const uint32_t* tmask, 
           if (pos < cap) put(pos, lo, hi, im);
           ++pos;
         }
-      }, mark);
+      }, lane_mark);
     }
     n_seeds += n_kept;
     n_done += count;

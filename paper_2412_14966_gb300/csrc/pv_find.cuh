@@ -21,7 +21,9 @@ using namespace pvdev;
 // uni     during the fill: the prepared tracks of a fill pass (kFillChunk
 //         records of 16 bytes); afterwards: the association's arrays and the
 //         per-round vertex counts of the placement
-// mark    the recursive dip split's pending right-hand sides (x86 flavour)
+// mark    inside uni, after the tile masks: the recursive dip split's
+//         pending right-hand sides (x86 flavour; mark_cap int16 entries,
+//         shared out among the proto-clusters during the peak search)
 
 constexpr int kFillChunk = 256;             // most tracks one fill pass prepares
 constexpr int kPlaceRounds = kSmallCap / 32;
@@ -33,11 +35,13 @@ __host__ __device__ constexpr int fill_per_thread(int nt) { return nt >= 256 ? 1
 
 struct Layout {
   size_t hist, tmask, seeds, ring, misc, center, cid, uni, mark, total;
+  int mark_cap;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// rec: the recursive (x86) dip split, which keeps one int16 per bin (mark)
+// (rec, the recursive (x86) dip split, needs no memory of its own: its
+// scratch lies in uni; the argument is kept for the callers)
 __host__ __device__ inline Layout make_layout(int nbins, int mode, int nt, bool rec = false) {
   Layout L;
   size_t o = 0;
@@ -52,8 +56,12 @@ __host__ __device__ inline Layout make_layout(int nbins, int mode, int nt, bool 
   L.misc = o;   o += sizeof(int) * kMiscInts;
   L.center = o; o += sizeof(int16_t) * kSmallCap;
   L.cid = o;    o += align_up(sizeof(int8_t) * kSmallCap, 16);
-  L.uni = o;    o += align_up(recs > assoc ? recs : assoc, 16);
-  L.mark = o;   o += (find && rec) ? align_up(sizeof(int16_t) * ntiles * 32, 16) : 0;
+  const size_t uni = align_up(recs > assoc ? recs : assoc, 16);
+  const size_t tiles = 2 * sizeof(uint32_t) * kTileWords * 32;   // the peak search's tile masks
+  L.uni = o;    o += uni;
+  L.mark = L.uni + tiles;
+  L.mark_cap = (find && uni > tiles) ? static_cast<int>((uni - tiles) / sizeof(int16_t)) : 0;
+  (void)rec;
   L.total = align_up(o, 16);
   return L;
 }
@@ -105,25 +113,27 @@ __device__ __forceinline__ void warp_place(const CidT* cid, int n, int* base, Sl
 }
 
 // Step (c) with the whole CTA, on the shared histogram N of one event (whole
-// 32-bin tiles).  Every warp scans its share of the
-// touched tiles and records, per tile, the bins where a run of bins above
-// the threshold starts and ends (smask, emask); warp 0 lists the runs in z
-// order (r_lo, r_hi: NT entries each); thread r walks run r (the proto-cluster)
-// and counts its kept pieces, keeping the first two; a
-// block-wide scan of the counts gives each piece its seed index.  Writes up to
-// cap seeds into S in z order and returns their number (which may exceed
-// cap) on every thread, or -1 on every thread when the event has more runs
-// than threads (the caller then runs the one-warp search).  misc_scan: NT/32
-// ints; misc_n: one int; mark: the recursive split's per-bin scratch.  All
-// threads of the CTA must call it.
+// 32-bin tiles).  Every warp scans its share of the touched tiles and records,
+// per tile, the bins where a run of bins above the threshold starts and ends
+// (smask, emask); warp 0 lists the runs in z order (r_lo, r_hi: NT entries
+// each); thread r walks run r (the proto-cluster) and counts its kept pieces,
+// keeping the first two; a block-wide scan of the counts gives each piece its
+// seed index.  Writes up to cap seeds into S in z order and returns their
+// number (which may exceed cap) on every thread, or -1 on every thread when
+// the event has more runs than threads (the caller then runs the one-warp
+// search).  misc_scan: 2 NT/32 ints; misc_n: one int; mark: mark_cap entries
+// of scratch for the recursive split, shared out among the proto-clusters
+// (one whose share does not fit splits without scratch).  All threads of the
+// CTA must call it.
 template <int kSplit, int NT>
 __device__ int block_find_seeds(const uint32_t* N, const uint32_t* tmask, const Consts& C,
                                 SeedOut* S, int cap, uint32_t* smask, uint32_t* emask,
                                 int16_t* r_lo, int16_t* r_hi, int* misc_scan, int* misc_n,
-                                int16_t* mark) {
+                                int16_t* mark, int mark_cap) {
   constexpr int NW = NT / 32;
   static_assert(kTileWords * 32 <= 4 * 32, "the run list covers at most 128 tiles");
   static_assert(2 * kRunRing * NW >= 2 * NT, "the run list lives in the proto-cluster rings");
+  static_assert(kMiscWarpScan + 2 * NW <= kMiscInts, "two per-warp scans in misc");
   static_assert(sizeof(float4) * kFillChunk >= 2 * sizeof(uint32_t) * kTileWords * 32,
                 "the tile masks live in the fill records");
   const int tid = threadIdx.x;
@@ -219,8 +229,27 @@ __device__ int block_find_seeds(const uint32_t* N, const uint32_t* tmask, const 
     for (int i = a; i <= b; ++i) total += N[i];
   }
   const uint64_t t_min = C.t_pp < C.t_gas ? C.t_pp : C.t_gas;
+  const bool walk = b >= a && total >= t_min;
+  // each walked proto-cluster's share of the scratch (recursive split): a
+  // block-wide scan of their lengths
+  int16_t* my_mark = nullptr;
+  if constexpr (kSplit == PV_SPLIT_RECURSIVE) {
+    const int len = walk ? b - a + 1 : 0;
+    int end = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, end, o);
+      if (lane >= o) end += v;
+    }
+    if (lane == 31) misc_scan[NW + warp] = end;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < NW; ++w)
+      if (w < warp) end += misc_scan[NW + w];
+    if (walk && end <= mark_cap) my_mark = mark + (end - len);
+  }
   int kept = 0, lo1 = 0, hi1 = 0, im1 = 0, lo2 = 0, hi2 = 0, im2 = 0;
-  if (b >= a && total >= t_min) {
+  if (walk) {
     split_pieces<kSplit>(N, a, b, total, C,
                          [&](int lo, int hi, uint64_t integral, int im) {
       if (keep_piece(integral, im, C)) {
@@ -231,7 +260,7 @@ __device__ int block_find_seeds(const uint32_t* N, const uint32_t* tmask, const 
         }
         ++kept;
       }
-    }, mark);
+    }, my_mark);
   }
   // each piece's index: exclusive scan of the counts in run order
   int incl = kept;
@@ -260,7 +289,7 @@ __device__ int block_find_seeds(const uint32_t* N, const uint32_t* tmask, const 
         if (pos < cap) put_seed(N, C, S, pos, lo, hi, im);
         ++pos;
       }
-    }, mark);
+    }, my_mark);
   }
   return n_kept;
 }
@@ -579,15 +608,17 @@ __device__ __forceinline__ void find_event(const Consts& C, const TrackPtrs& T, 
 
       // ---- (c): seeds from the touched tiles, with the whole CTA (with warp
       // 0 alone when the event has more runs than threads)
-      int16_t* mark = reinterpret_cast<int16_t*>(smem + Lo.mark);
+      int16_t* mark = reinterpret_cast<int16_t*>(smem + Lo.mark);   // (x86 flavour)
       int16_t* runs = reinterpret_cast<int16_t*>(smem + Lo.ring);
       uint32_t* tiles = reinterpret_cast<uint32_t*>(smem + Lo.uni);
       int Kall = block_find_seeds<SPLIT, NT>(hist, tmask, C, S, O.cap, tiles,
                                              tiles + kTileWords * 32, runs, runs + NT,
-                                             misc + kMiscWarpScan, misc + kMiscFlag, mark);
+                                             misc + kMiscWarpScan, misc + kMiscFlag, mark,
+                                             Lo.mark_cap);
       if (Kall < 0) {
         if (warp == 0) {
-          const int K = warp_find_seeds<false, SPLIT>(hist, tmask, C, S, O.cap, pc_lo, pc_hi, mark);
+          const int K = warp_find_seeds<false, SPLIT>(hist, tmask, C, S, O.cap, pc_lo, pc_hi, mark,
+                                                      Lo.mark_cap);
           if (lane == 0) misc[kMiscK] = K;
         }
         __syncthreads();

@@ -937,7 +937,8 @@ plain_peaks_kernel(Consts C, TrackPtrs T, const uint32_t* hist, int cap, int32_t
     return;
   }
   int K = warp_find_seeds<true, SPLIT>(hist + static_cast<size_t>(e) * C.nbins, nullptr, C, &S,
-                                       cap, pc_lo, pc_hi, mark);
+                                       cap, pc_lo, pc_hi, mark,
+                                       SPLIT == PV_SPLIT_RECURSIVE ? kMaxBins : 0);
   int Ks = K < cap ? K : cap;
   for (int k = lane; k < Ks; k += 32) {
     size_t q = static_cast<size_t>(e) * kMaxSeeds + k;

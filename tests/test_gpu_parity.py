@@ -471,3 +471,43 @@ def test_recursive_split_deep_comb_on_the_gpu(pv, path):
     s, v = G.gpu_find_fit(ctx, batch)
     ctx.close()
     G.assert_find_equal(s, ref, batch)
+
+
+def _long_event(n_broad=840, z0=-290.0, step=0.5, peaks=14):
+    """One event whose histogram is a single proto-cluster of about 1,700 bins:
+    broad pp tracks (sigma_poca 1.2 mm) every 0.5 mm over 420 mm lift every bin
+    above the threshold, and narrow peaks of 12 + k tracks every 29 mm split it."""
+    t = np.array([[0.3, 0.0]])
+    ev = []
+    for j in range(n_broad):
+        z = z0 + step * j
+        ev.append(synthetic.straight_tracks((0.0, 0.0, z), t, [z], cov_xx=(1.2 * 0.3) ** 2,
+                                            cov_tt=1e-14))
+    for k in range(peaks):
+        z = z0 + 15.0 + 29.0 * k + 0.125
+        m = 12 + k
+        ev.append(synthetic.straight_tracks((0.0, 0.0, z), np.repeat(t, m, 0), np.full(m, z),
+                                            cov_xx=(0.05 * 0.3) ** 2, cov_tt=1e-14))
+    return {k: np.concatenate([e[k] for e in ev]) for k in synthetic.TRACK_FIELDS}
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_recursive_split_longer_than_its_scratch_on_the_gpu(pv, path):
+    """The recursive split's scratch in the find kernel holds 1,536 bins of
+    proto-clusters; a longer one splits without scratch (each piece found by
+    descending from the top), one that still fits beside it with: seeds,
+    bounds and assignments bit-exact with the oracle either way."""
+    batch = synthetic.batch_from_events([_long_event(), _comb_event(), _long_event(peaks=9),
+                                         _comb_event(25, rising=False)])
+    p = oracle.default_params(split_mode=1)
+    ref = oracle.find_batch(batch, p, want_hist=True)
+    h = ref["hist"][0]
+    above = h > p.bin_threshold
+    assert int(above.sum()) > 1536 and ref["n"][0] == 14
+    cfg = dict(split_mode=pv.SPLIT_RECURSIVE)
+    if path == "plain":
+        cfg["path"] = pv.PATH_PLAIN
+    ctx = pv.Context(device=0, **cfg)
+    s, v = G.gpu_find_fit(ctx, batch)
+    ctx.close()
+    G.assert_find_equal(s, ref, batch)

@@ -43,6 +43,7 @@ def _gpu_walk(lib, N, split_mode=0):
     n = lib.harness_seeds(N.ctypes.data_as(C.POINTER(C.c_uint32)), NB, P.bin_threshold, t_pp,
                           t_gas, P.dip_num, P.dip_den, oracle.gas_bin(P), split_mode, ip(lo),
                           ip(hi), ip(bn), cap)
+    assert n >= 0, "the recursive split with and without its scratch gives different pieces"
     return list(zip(lo[:n].tolist(), hi[:n].tolist(), bn[:n].tolist()))
 
 
