@@ -158,6 +158,7 @@ serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
   const Layout Lo = make_layout(C.nbins, kFindFit, NT, flavour_split(FLAV) == PV_SPLIT_RECURSIVE);
   find_prologue<kFindFit, NT>(C, smem, Lo);
   __shared__ ServeDesc s_d;
+  __shared__ TrackScratch s_G;       // the request's scratch, from s_d
   __shared__ ServeQueue Q;
   __shared__ unsigned long long s_g;
   __shared__ int s_code, s_round;
@@ -278,6 +279,14 @@ serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
       if (threadIdx.x == 0) {
         s_code = code;
         // the event's request: a queue entry (a new one unless the last is it)
+        if (code < 0) {
+          s_G = TrackScratch{};
+          s_G.center = s_d.center;
+          s_G.cid = s_d.cid;
+          s_G.slot = s_d.slot;
+          s_G.A = s_d.A;
+          s_G.W = s_d.W;
+        }
         if (code < 0 && (Q.nreq == 0 || Q.req[Q.nreq - 1].seq != s_d.seq) &&
             PV_CHECK(Q.nreq < kServeReqs, 22)) {
           ServeReq& R = Q.req[Q.nreq];
@@ -294,17 +303,11 @@ serve_kernel(Consts C, ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
     }
     __syncthreads();
     if (s_code >= 0) break;
-    const TrackPtrs T = s_d.T;
-    const OutPtrs O = s_d.O;
+    // (the event's pointers are read from the shared descriptor where they are
+    // used: warp 0 rewrites it only after the event)
     const int e = static_cast<int>(s_g - s_d.ev_base);
-    TrackScratch G{};
-    G.center = s_d.center;
-    G.cid = s_d.cid;
-    G.slot = s_d.slot;
-    G.A = s_d.A;
-    G.W = s_d.W;
-    __syncthreads();                 // s_d may change once thread 0 claims again
-    find_event<kFindFit | kServe, NT, FLAV>(C, T, SeedPtrs{}, O, G, smem, e, nullptr, 0, &Q);
+    find_event<kFindFit | kServe, NT, FLAV>(C, s_d.T, SeedPtrs{}, s_d.O, s_G, smem, e, nullptr, 0,
+                                            &Q);
     __syncthreads();
     if (threadIdx.x == 0) Q.req[Q.nreq - 1].events += 1;
   }
