@@ -611,10 +611,25 @@ def run_ours(args):
         be_.record(stream)
         torch.cuda.synchronize()
         b_ms = bs_.elapsed_time(be_) / b_steps
+        # the autotuner's choice for the other event-size buckets, on samples of
+        # their sizes (pv_autotune keeps one launch shape per bucket)
+        per_bucket = {"below 300 tracks/event (this mixture, %.0f on average)"
+                      % (mix.n_tracks / mix.n_events): {"find_threads": mlaunch[0],
+                                                        "fit_threads": mlaunch[1]}}
+        for label, mu, seed in (("300 to 800 tracks/event (pile-up mu 15)", 15.0, 11),
+                                ("800 tracks/event and more (pile-up mu 40)", 40.0, 12)):
+            smp = synthetic.generate(1000, seed, mu=mu, mean_tracks=28.0, name=f"pileup-{mu:.0f}")
+            st_ = pv.Tracks.from_batch(smp)
+            so_ = pv.Vertices.empty(smp.n_events, smp.n_tracks)
+            sh = mctx.autotune(st_, so_, stream=stream)
+            per_bucket[label + ", %.0f on average" % (smp.n_tracks / smp.n_events)] = {
+                "find_threads": sh[0], "fit_threads": sh[1]}
+            del st_, so_, smp
         batched = {"value": mix.n_events / (b_ms / 1e3), "ms_per_step": b_ms,
                    "events": mix.n_events, "tracks": mix.n_tracks,
                    "input_gb": round(mix.n_tracks * 44 / 1e9, 3),
                    "launch": {"find_threads": mlaunch[0], "fit_threads": mlaunch[1]},
+                   "launch_per_bucket": per_bucket,
                    "workload": "mixture: 200,000 events, mu ~ U(1,12) per event, 20% fixed-target"}
         mctx.close()
         del mt, mo, mix
