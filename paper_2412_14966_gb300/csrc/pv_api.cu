@@ -933,6 +933,7 @@ int pv_fit_multi(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
   const size_t o_cnt = o; o += 256;
   const size_t o_K = o; o += round16(sizeof(int) * E);
   const size_t o_P = o; o += round16(3 * sizeof(float4) * n);
+  const size_t o_tev = o; o += round16(sizeof(int) * n);
   const size_t o_work = o; o += round16(sizeof(int2) * slots);
   const size_t o_redo = o; o += round16(sizeof(int2) * slots);
   const size_t o_sx = o; o += round16(sizeof(float) * slots);
@@ -950,6 +951,7 @@ int pv_fit_multi(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
   M.counters = reinterpret_cast<int*>(base + o_cnt);
   M.K = reinterpret_cast<int*>(base + o_K);
   M.P = reinterpret_cast<float4*>(base + o_P);
+  M.tev = reinterpret_cast<int*>(base + o_tev);
   M.work = reinterpret_cast<int2*>(base + o_work);
   M.redo = reinterpret_cast<int2*>(base + o_redo);
   M.sx = reinterpret_cast<float*>(base + o_sx);

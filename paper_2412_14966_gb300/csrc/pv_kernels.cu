@@ -188,10 +188,9 @@ __device__ __forceinline__ float mv_seed_term(float X, float Y, float wx, float 
   return __expf(-0.5f * (X * X * wx + Y * Y * wy));
 }
 
-// p: the track's packed record (three float4, written by mv_seed_kernel).
-__device__ __forceinline__ bool mv_track(const float4* p, float xs, float ys, float zs,
-                                         MvTrack* m) {
-  const float4 a = p[0], b = p[1], c4 = p[2];
+// a, b, c4: the track's packed record (three float4, written by mv_seed_kernel).
+__device__ __forceinline__ bool mv_track_rec(const float4& a, const float4& b, const float4& c4,
+                                             float xs, float ys, float zs, MvTrack* m) {
   float4 A;
   float2 W;
   make_fit_track(a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c4.x, c4.y, c4.z, xs, ys, zs, &A, &W);
@@ -200,6 +199,10 @@ __device__ __forceinline__ bool mv_track(const float4* p, float xs, float ys, fl
   const float c = c4.w - mv_seed_term(A.x, A.y, W.x, W.y);
   m->comp = c > 0.0f ? c : 0.0f;
   return true;
+}
+__device__ __forceinline__ bool mv_track(const float4* p, float xs, float ys, float zs,
+                                         MvTrack* m) {
+  return mv_track_rec(p[0], p[1], p[2], xs, ys, zs, m);
 }
 
 __device__ __forceinline__ float mv_weight(float c2, float comp, const Consts& C) {
@@ -373,14 +376,17 @@ __device__ void group_fit_multi(const float4* rec, int n, const int16_t* list, f
   out->status = status == 0 ? PV_ST_MAXITER : status;
 }
 
-// The multi-vertex fit runs as three kernels:
-//   mv_seed_kernel   one warp per event: each track's packed record with its
-//                    seed sum S (global) and one work item (event, vertex) per
-//                    seed;
-//   mv_fit_kernel    persistent, four vertices per warp from the work list,
-//                    any event: the fits (group_fit_multi);
-//   mv_final_kernel  one warp per event: each track's vertex from the last-
-//                    iteration weights, duplicates in seed order, selection.
+// The multi-vertex fit runs as five kernels:
+//   mv_seed_kernel    one warp per event: each track's packed record with its
+//                     seed sum S (global) and event, one work item (event,
+//                     vertex) per seed;
+//   mv_fit_kernel     persistent, four vertices per warp from the work list,
+//                     any event: the fits over the vertices' windows, then
+//                     the refits over all tracks (group_fit_multi);
+//   mv_assign_kernel  one thread per track: its vertex from the last-
+//                     iteration weights;
+//   mv_select_kernel  one thread per event: duplicates in seed order,
+//                     selection.
 
 __global__ void __launch_bounds__(kMvThreads)
 mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
@@ -444,6 +450,7 @@ mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
       q[0] = make_float4(x, y, z, tx);
       q[1] = make_float4(ty, a, b, c);
       q[2] = make_float4(d, f, g, sum);
+      M.tev[i] = e;
     }
   }
   // work items: one per seed
@@ -561,60 +568,66 @@ mv_fit_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
   }
 }
 
-// Each track's vertex, then duplicates and the final selection; one warp per
-// event.
-__global__ void __launch_bounds__(kMvThreads)
-mv_final_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
-  const int lane = threadIdx.x & 31;
-  const int e = (blockIdx.x * kMvThreads + threadIdx.x) >> 5;
+// Each track's vertex: the vertex of its largest last-iteration weight if
+// that is at least mv_w_assoc (the lowest index on ties), else none; one thread
+// per track (tracks of events with bad offsets carry no event and are left
+// alone).
+__global__ void __launch_bounds__(256)
+mv_assign_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= T.n_tracks) return;
+  const int e = M.tev[i];
+  if (e < 0 || e >= T.n_events) return;
+  const int K = M.K[e];
+  const size_t s0 = static_cast<size_t>(e) * kMaxSeeds;
+  const float4* p = M.P + 3 * i;
+  const float4 ra = p[0], rb = p[1], rc = p[2];
+  int best = -1;
+  float wbest = -1.0f;
+  for (int j = 0; j < K; ++j) {
+    if (M.vst[s0 + j] & PV_ST_SINGULAR) continue;
+    MvTrack m;
+    if (!mv_track_rec(ra, rb, rc, M.sx[s0 + j], M.sy[s0 + j], M.sz[s0 + j], &m)) continue;
+    const float w = mv_weight(mv_chi2_at(m, M.last[s0 + j]), m.comp, C);
+    if (w > wbest) {
+      wbest = w;
+      best = j;
+    }
+  }
+  O.track_vertex[i] = (best >= 0 && wbest >= C.mv_w_assoc) ? best : -1;
+}
+
+// Duplicates in seed order, then the final selection; one thread per event.
+__global__ void __launch_bounds__(256)
+mv_select_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= T.n_events) return;
   const int K = M.K[e];
-  const int64_t b0 = T.off[e], b1 = T.off[e + 1];
-  if (offsets_bad(b0, b1, T.n_tracks)) return;
-  const int n = static_cast<int>(b1 - b0);
   const size_t s0 = static_cast<size_t>(e) * kMaxSeeds;
-  for (int t = lane; t < n; t += 32) {
-    int best = -1;
-    float wbest = -1.0f;
-    for (int j = 0; j < K; ++j) {
-      if (M.vst[s0 + j] & PV_ST_SINGULAR) continue;
-      MvTrack m;
-      if (!mv_track(M.P + 3 * (b0 + t), M.sx[s0 + j], M.sy[s0 + j], M.sz[s0 + j], &m))
-        continue;
-      const float w = mv_weight(mv_chi2_at(m, M.last[s0 + j]), m.comp, C);
-      if (w > wbest) {
-        wbest = w;
-        best = j;
-      }
-    }
-    O.track_vertex[b0 + t] = (best >= 0 && wbest >= C.mv_w_assoc) ? best : -1;
-  }
-  if (lane == 0) {
-    int kept = -1;
-    for (int j = 0; j < K; ++j) {
-      int st = M.vst[s0 + j];
-      if (st & PV_ST_SINGULAR) continue;
-      if (kept >= 0) {
-        const float dz = M.vz[s0 + j] - M.vz[s0 + kept];
-        if (dz * dz < C.mv_dup_sep2 * (M.vczz[s0 + j] + M.vczz[s0 + kept])) {
-          if (M.vn[s0 + j] > M.vn[s0 + kept]) {
-            M.vst[s0 + kept] |= PV_ST_DUPLICATE;
-            kept = j;
-          } else {
-            M.vst[s0 + j] |= PV_ST_DUPLICATE;
-          }
-          continue;
+  int kept = -1;
+  for (int j = 0; j < K; ++j) {
+    int st = M.vst[s0 + j];
+    if (st & PV_ST_SINGULAR) continue;
+    if (kept >= 0) {
+      const float dz = M.vz[s0 + j] - M.vz[s0 + kept];
+      if (dz * dz < C.mv_dup_sep2 * (M.vczz[s0 + j] + M.vczz[s0 + kept])) {
+        if (M.vn[s0 + j] > M.vn[s0 + kept]) {
+          M.vst[s0 + kept] |= PV_ST_DUPLICATE;
+          kept = j;
+        } else {
+          M.vst[s0 + j] |= PV_ST_DUPLICATE;
         }
+        continue;
       }
-      kept = j;
     }
-    for (int j = 0; j < K; ++j) {
-      const size_t q = static_cast<size_t>(e) * O.cap + j;
-      int st = M.vst[s0 + j];
-      if (!(st & (PV_ST_SINGULAR | PV_ST_DUPLICATE)))
-        st = select_vertex(O.x[q], O.y[q], M.vz[s0 + j], M.vn[s0 + j], st, C);
-      if (O.status) O.status[q] = st;
-    }
+    kept = j;
+  }
+  for (int j = 0; j < K; ++j) {
+    const size_t q = static_cast<size_t>(e) * O.cap + j;
+    int st = M.vst[s0 + j];
+    if (!(st & (PV_ST_SINGULAR | PV_ST_DUPLICATE)))
+      st = select_vertex(O.x[q], O.y[q], M.vz[s0 + j], M.vn[s0 + j], st, C);
+    if (O.status) O.status[q] = st;
   }
 }
 
@@ -625,11 +638,16 @@ cudaError_t launch_mv_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S
   if (err != cudaSuccess) return err;
   const int per_block = kMvThreads / 32;
   const int grid = (T.n_events + per_block - 1) / per_block;
+  // (tracks of events the seed kernel skips keep event -1)
+  err = cudaMemsetAsync(M.tev, 0xff, sizeof(int) * static_cast<size_t>(T.n_tracks), st);
+  if (err != cudaSuccess) return err;
   mv_seed_kernel<<<grid, kMvThreads, 0, st>>>(C, T, S, O, M);
   mv_fit_kernel<false><<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
   mv_fit_kernel<true><<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
-  mv_final_kernel<<<grid, kMvThreads, 0, st>>>(C, T, O, M);
-  *n_launches += 4;
+  if (T.n_tracks > 0)
+    mv_assign_kernel<<<static_cast<unsigned>((T.n_tracks + 255) / 256), 256, 0, st>>>(C, T, O, M);
+  mv_select_kernel<<<(T.n_events + 255) / 256, 256, 0, st>>>(C, T, O, M);
+  *n_launches += 5;
   return cudaGetLastError();
 }
 

@@ -246,6 +246,7 @@ struct MvScratch {
   int* counters;            // [0] work items listed, [1] next item to fit, [2] vertices
                             // listed for a refit over all tracks, [3] next one to refit
   int* K;                   // per event: seeds fitted
+  int* tev;                 // per track: its event (-1: none)
   float4* P;                // per track, three float4: x y z tx | ty cxx cxtx ctxtx |
                             // cyy cyty ctyty S, S = sum over the event's seeds of exp(-chi2/2)
   int2* work;               // (event, seed) per vertex
