@@ -188,7 +188,7 @@ __device__ __forceinline__ float mv_seed_term(float X, float Y, float wx, float 
   return __expf(-0.5f * (X * X * wx + Y * Y * wy));
 }
 
-// a, b, c4: the track's packed record (three float4, written by mv_seed_kernel).
+// a, b, c4: the track's packed record (three float4, written by mv_sums_kernel).
 __device__ __forceinline__ bool mv_track_rec(const float4& a, const float4& b, const float4& c4,
                                              float xs, float ys, float zs, MvTrack* m) {
   float4 A;
@@ -376,10 +376,11 @@ __device__ void group_fit_multi(const float4* rec, int n, const int16_t* list, f
   out->status = status == 0 ? PV_ST_MAXITER : status;
 }
 
-// The multi-vertex fit runs as five kernels:
-//   mv_seed_kernel    one warp per event: each track's packed record with its
-//                     seed sum S (global) and event, one work item (event,
-//                     vertex) per seed;
+// The multi-vertex fit runs as six kernels:
+//   mv_event_kernel   one warp per event: its seeds, one work item (event,
+//                     vertex) per seed, each track's event;
+//   mv_sums_kernel    one thread per track: its packed record with its seed
+//                     sum S;
 //   mv_fit_kernel     persistent, four vertices per warp from the work list,
 //                     any event: the fits over the vertices' windows, then
 //                     the refits over all tracks (group_fit_multi);
@@ -389,7 +390,7 @@ __device__ void group_fit_multi(const float4* rec, int n, const int16_t* list, f
 //                     selection.
 
 __global__ void __launch_bounds__(kMvThreads)
-mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
+mv_event_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
   const int lane = threadIdx.x & 31;
   const int e = (blockIdx.x * kMvThreads + threadIdx.x) >> 5;
   if (e >= T.n_events) return;                       // whole warps
@@ -427,32 +428,8 @@ mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
     const size_t q = static_cast<size_t>(e) * kMaxSeeds + lane + 32;
     M.sx[q] = sx1; M.sy[q] = sy1; M.sz[q] = sz1;
   }
-  for (int t0 = 0; t0 < n; t0 += 32) {        // warp-uniform: the loop shuffles
-    const int t = t0 + lane;
-    const bool valid = t < n;
-    const int64_t i = b0 + (valid ? t : 0);
-    const float x = T.x[i], y = T.y[i], z = T.z[i], tx = T.tx[i], ty = T.ty[i];
-    const float a = T.cxx[i], b = T.cxtx[i], c = T.ctxtx[i];
-    const float d = T.cyy[i], f = T.cyty[i], g = T.ctyty[i];
-    float sum = 0.f;
-    for (int k = 0; k < K; ++k) {
-      const int src = k & 31;
-      const float kx = __shfl_sync(0xffffffffu, k < 32 ? sx0 : sx1, src);
-      const float ky = __shfl_sync(0xffffffffu, k < 32 ? sy0 : sy1, src);
-      const float kz = __shfl_sync(0xffffffffu, k < 32 ? sz0 : sz1, src);
-      float4 A;
-      float2 W;
-      make_fit_track(x, y, z, tx, ty, a, b, c, d, f, g, kx, ky, kz, &A, &W);
-      if (W.x > 0.0f) sum += mv_seed_term(A.x, A.y, W.x, W.y);
-    }
-    if (valid) {
-      float4* q = M.P + 3 * i;
-      q[0] = make_float4(x, y, z, tx);
-      q[1] = make_float4(ty, a, b, c);
-      q[2] = make_float4(d, f, g, sum);
-      M.tev[i] = e;
-    }
-  }
+  // each track's event (the sums follow, one thread per track)
+  for (int t = lane; t < n; t += 32) M.tev[b0 + t] = e;
   // work items: one per seed
   int wb = 0;
   if (lane == 0) {
@@ -463,6 +440,33 @@ mv_seed_kernel(Consts C, TrackPtrs T, SeedPtrs SP, OutPtrs O, MvScratch M) {
   wb = __shfl_sync(0xffffffffu, wb, 0);
   for (int k = lane; k < K; k += 32)
     if (PV_CHECK(K <= kMaxSeeds, 13)) M.work[wb + k] = make_int2(e, k);
+}
+
+// Each track's packed record with its seed sum S = sum over the event's seeds
+// (in seed order) of exp(-chi2/2) at the seed; one thread per track.
+__global__ void __launch_bounds__(256)
+mv_sums_kernel(Consts C, TrackPtrs T, MvScratch M) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= T.n_tracks) return;
+  const int e = M.tev[i];
+  if (e < 0 || e >= T.n_events) return;
+  const int K = M.K[e];
+  const size_t s0 = static_cast<size_t>(e) * kMaxSeeds;
+  const float x = T.x[i], y = T.y[i], z = T.z[i], tx = T.tx[i], ty = T.ty[i];
+  const float a = T.cxx[i], b = T.cxtx[i], c = T.ctxtx[i];
+  const float d = T.cyy[i], f = T.cyty[i], g = T.ctyty[i];
+  float sum = 0.f;
+  for (int k = 0; k < K; ++k) {
+    float4 A;
+    float2 W;
+    make_fit_track(x, y, z, tx, ty, a, b, c, d, f, g, M.sx[s0 + k], M.sy[s0 + k], M.sz[s0 + k],
+                   &A, &W);
+    if (W.x > 0.0f) sum += mv_seed_term(A.x, A.y, W.x, W.y);
+  }
+  float4* q = M.P + 3 * i;
+  q[0] = make_float4(x, y, z, tx);
+  q[1] = make_float4(ty, a, b, c);
+  q[2] = make_float4(d, f, g, sum);
 }
 
 // Multi-vertex fits from the work list: every 8-lane group fits one vertex.
@@ -638,16 +642,18 @@ cudaError_t launch_mv_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S
   if (err != cudaSuccess) return err;
   const int per_block = kMvThreads / 32;
   const int grid = (T.n_events + per_block - 1) / per_block;
-  // (tracks of events the seed kernel skips keep event -1)
+  // (tracks of events the event kernel skips keep event -1)
   err = cudaMemsetAsync(M.tev, 0xff, sizeof(int) * static_cast<size_t>(T.n_tracks), st);
   if (err != cudaSuccess) return err;
-  mv_seed_kernel<<<grid, kMvThreads, 0, st>>>(C, T, S, O, M);
+  mv_event_kernel<<<grid, kMvThreads, 0, st>>>(C, T, S, O, M);
+  if (T.n_tracks > 0)
+    mv_sums_kernel<<<static_cast<unsigned>((T.n_tracks + 255) / 256), 256, 0, st>>>(C, T, M);
   mv_fit_kernel<false><<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
   mv_fit_kernel<true><<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
   if (T.n_tracks > 0)
     mv_assign_kernel<<<static_cast<unsigned>((T.n_tracks + 255) / 256), 256, 0, st>>>(C, T, O, M);
   mv_select_kernel<<<(T.n_events + 255) / 256, 256, 0, st>>>(C, T, O, M);
-  *n_launches += 5;
+  *n_launches += 6;
   return cudaGetLastError();
 }
 
