@@ -38,7 +38,7 @@ BYTES_PER_TRACK = 48     # 11 input floats + the track's vertex index
 BYTES_PER_VERTEX = 56    # position, covariance, chi2, ndof, counts, status
 BYTES_PER_EVENT = 8      # CSR offset
 N_REPLICAS = 4           # rotating input copies: 4 x 70 MB > 129 MB L2
-SERVE_SWEEP = (1e6, 5e6, 20e6, 30e6, 50e6)   # offered events/s of the serving sweep
+SERVE_SWEEP = (1e6, 2e6, 5e6, 20e6, 30e6, 50e6)   # offered events/s of the serving sweep
 
 
 def _peaks():
