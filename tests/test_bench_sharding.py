@@ -71,3 +71,16 @@ def test_two_gloo_ranks_shard_and_aggregate(tmp_path):
         sl = slice(i * N_EV, (i + 1) * N_EV)
         assert np.array_equal(fit["z"][sl, :k], r[i]["vz"])
         assert np.array_equal(fit["x"][sl, :k], r[i]["vx"])
+
+
+def test_reference_worker_takes_a_bounded_sample():
+    """A reference-arm worker processes the first `take` events of its range
+    (its whole range when take is None), reps times, and counts them."""
+    sys.path.insert(0, ROOT)
+    import bench
+    oracle.build()
+    bench._pool_init(2, N_EV)
+    half = N_EV // 2
+    assert bench._pool_run((0, 1, None)) == half
+    assert bench._pool_run((1, 2, 3)) == 6
+    assert bench._pool_run((1, 1, 10 * N_EV)) == half
