@@ -388,8 +388,8 @@ __device__ __forceinline__ bool offsets_bad(int64_t b0, int64_t b1, int64_t n_tr
 //          evenly over the threads, each walking its range of consecutive
 //          items (one CDF per item, the right edge carried over as the next
 //          bin's left edge)
-//   peaks  warp 0 scans the touched tiles (ballots) and walks the
-//          proto-clusters, one per lane
+//   peaks  every warp scans its share of the touched tiles, warp 0 lists the
+//          runs, thread r walks run r (warp 0 alone beyond NT runs)
 //   assoc  block-cooperative association with the removal loop
 //   place  per 32-track round, the tracks of each vertex are ranked with
 //          __match_any_sync and the rounds' counts summed, giving each track
