@@ -233,7 +233,7 @@ struct pv_ctx {
   };
   std::map<cudaStream_t, StreamWs> ws;
   DevBuf tpl;                         // template profiles (profile_mode TEMPLATE)
-  int mv_per_sm = 0;
+  int mv_per_sm = 0, mv_redo_per_sm = 0;
   // host-buffer entry point staging
   DevBuf host_in, host_out;
   cudaStream_t own_stream = nullptr;
@@ -811,7 +811,8 @@ int pv_init(const pv_config* cfg, const pv_beamline* beam, int device, pv_ctx** 
   for (int k = 0; k < 3; ++k)
     for (int i = 0; i < 2; ++i) ctx->fit_per_sm[k][i] = pvk::fit_blocks_per_sm(k, i == 0 ? 128 : 256);
   for (int b = 0; b < 3; ++b) ctx->bucket_cfg[b] = pvk::LaunchCfg{128, 0, pvk::kFitThreads, 0};
-  ctx->mv_per_sm = pvk::mv_blocks_per_sm();
+  ctx->mv_per_sm = pvk::mv_blocks_per_sm(false);
+  ctx->mv_redo_per_sm = pvk::mv_blocks_per_sm(true);
   *out = ctx;
   return PV_OK;
 }
@@ -963,9 +964,10 @@ int pv_fit_multi(pv_ctx* ctx, const pv_tracks* tracks, const pv_vertices* seeds,
   M.vn = reinterpret_cast<int*>(base + o_vn);
   M.vst = reinterpret_cast<int*>(base + o_vst);
   const int fit_grid = ctx->n_sm * (ctx->mv_per_sm > 0 ? ctx->mv_per_sm : 1);
+  const int redo_grid = ctx->n_sm * (ctx->mv_redo_per_sm > 0 ? ctx->mv_redo_per_sm : 1);
   int launches = 0;
   PV_CUDA(ctx, pvk::launch_mv_fit(ctx->C, track_ptrs(tracks), seed_ptrs(seeds), out_ptrs(out), M,
-                                  fit_grid, st, &launches));
+                                  fit_grid, redo_grid, st, &launches));
   ctx->launches += launches;
   return PV_OK;
 }

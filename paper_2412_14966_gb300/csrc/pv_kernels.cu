@@ -228,6 +228,9 @@ __device__ __forceinline__ float mv_chi2_at(const MvTrack& m, const MvLast& L) {
 constexpr float kMvWin = 200.0f;
 constexpr float kMvSafe = 60.0f;
 constexpr int kMvList = 128;           // most tracks a vertex's window holds
+constexpr int kMvRefitAhead = 2;       // tracks a lane loads ahead in a refit
+constexpr int kMvWindowBlocks = 4;     // CTAs per SM of the window fits
+constexpr int kMvRefitBlocks = 2;      // CTAs per SM of the refits
 
 // Multi-vertex fit of one vertex per G-lane group (binary32 sums), over the
 // tracks of the event whose packed records start at rec: all n of them (list
@@ -253,7 +256,26 @@ __device__ __forceinline__ T lanes_sum(T v) {
   return v;
 }
 
-template <int G>
+// A lane's records of its next U tracks (s0, s0 + G, ...; those at or past
+// cnt are not loaded), loaded before any is used so that their loads overlap.
+template <int G, int U>
+__device__ __forceinline__ void mv_load(const float4* rec, const int16_t* list, int s0, int cnt,
+                                        float4 (&P)[U][3]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int s = s0 + u * G;
+    if (s < cnt) {
+      const float4* p = rec + 3 * (list ? static_cast<int>(list[s]) : s);
+      P[u][0] = p[0];
+      P[u][1] = p[1];
+      P[u][2] = p[2];
+    }
+  }
+}
+
+// U: tracks a lane loads ahead (their terms are still added one by one in
+// track order, so U does not change a result's bits).
+template <int G, int U = 1>
 __device__ void group_fit_multi(const float4* rec, int n, const int16_t* list, float xs,
                                 float ys, float zs, bool active, const Consts& C, VertexOut* out,
                                 MvLast* last, float i_xy = 0.f, float i_z = 0.f,
@@ -261,11 +283,15 @@ __device__ void group_fit_multi(const float4* rec, int n, const int16_t* list, f
   const int r = threadIdx.x & (G - 1);
   const int cnt = active ? n : 0;
   float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-  for (int s = r; s < cnt; s += G) {
-    MvTrack m;
-    const int t = list ? static_cast<int>(list[s]) : s;
-    if (!mv_track(rec + 3 * t, xs, ys, zs, &m)) continue;
-    m0 += m.wx; m1 += m.wx * m.tx; m2 += m.wy; m3 += m.wy * m.ty;
+  for (int s0 = r; s0 < cnt; s0 += U * G) {
+    float4 P[U][3];
+    mv_load<G, U>(rec, list, s0, cnt, P);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      MvTrack m;
+      if (s0 + u * G >= cnt || !mv_track_rec(P[u][0], P[u][1], P[u][2], xs, ys, zs, &m)) continue;
+      m0 += m.wx; m1 += m.wx * m.tx; m2 += m.wy; m3 += m.wy * m.ty;
+    }
   }
   m0 = lanes_sum<G>(m0); m1 = lanes_sum<G>(m1); m2 = lanes_sum<G>(m2); m3 = lanes_sum<G>(m3);
   float cx = m0 > 0.f ? m1 / m0 : 0.f;
@@ -292,23 +318,28 @@ __device__ void group_fit_multi(const float4* rec, int n, const int16_t* list, f
       }
     }
     if (!done) {
-      for (int s = r; s < cnt; s += G) {
-        MvTrack m;
-        const int t = list ? static_cast<int>(list[s]) : s;
-        if (!mv_track(rec + 3 * t, xs, ys, zs, &m)) continue;
-        const float dtx = m.tx - P.cx, dty = m.ty - P.cy;
-        const float rx = m.X + P.az * dtx - P.axp;
-        const float ry = m.Y + P.az * dty - P.ayp;
-        const float c2 = rx * rx * m.wx + ry * ry * m.wy;
-        const float w = mv_weight(c2, m.comp, C);
-        const float wx = w * m.wx, wy = w * m.wy;
-        v[0] += wx; v[1] += wy;
-        v[2] += wx * dtx; v[3] += wy * dty;
-        v[4] += wx * dtx * dtx + wy * dty * dty;
-        v[5] += wx * rx; v[6] += wy * ry;
-        v[7] += wx * dtx * rx + wy * dty * ry;
-        v[8] += w * c2; v[9] += w;
-        if (w >= C.mv_w_assoc) ++cnt_w;
+      for (int s0 = r; s0 < cnt; s0 += U * G) {
+        float4 R[U][3];
+        mv_load<G, U>(rec, list, s0, cnt, R);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          MvTrack m;
+          if (s0 + u * G >= cnt || !mv_track_rec(R[u][0], R[u][1], R[u][2], xs, ys, zs, &m))
+            continue;
+          const float dtx = m.tx - P.cx, dty = m.ty - P.cy;
+          const float rx = m.X + P.az * dtx - P.axp;
+          const float ry = m.Y + P.az * dty - P.ayp;
+          const float c2 = rx * rx * m.wx + ry * ry * m.wy;
+          const float w = mv_weight(c2, m.comp, C);
+          const float wx = w * m.wx, wy = w * m.wy;
+          v[0] += wx; v[1] += wy;
+          v[2] += wx * dtx; v[3] += wy * dty;
+          v[4] += wx * dtx * dtx + wy * dty * dty;
+          v[5] += wx * rx; v[6] += wy * ry;
+          v[7] += wx * dtx * rx + wy * dty * ry;
+          v[8] += w * c2; v[9] += w;
+          if (w >= C.mv_w_assoc) ++cnt_w;
+        }
       }
     }
 #pragma unroll
@@ -476,11 +507,16 @@ mv_sums_kernel(Consts C, TrackPtrs T, MvScratch M) {
 // within reach, the fit was singular, or the listed tracks' weights sum below
 // one half (ndof = 2 sum w - 3), where tracks left out would no longer be
 // negligible -- goes to the refit list instead of the outputs.  kRedo = true:
-// the refit list, each vertex over every track of its event.  The fits wait on
-// their track loads, so four CTAs per SM (64 registers, a few spilled) beat
-// two (97 registers): 1.30 ms against 1.56 ms per nominal step.
+// the refit list, each vertex over every track of its event.  The window fits
+// wait on their track loads, so four CTAs per SM (64 registers, a few
+// spilled) beat two (97 registers): 1.30 ms against 1.56 ms per nominal step.
+// The refits are few and long (the vertices of the largest events, over all
+// their tracks): their time is the tail of the longest ones with few warps
+// left, so they run two CTAs per SM with 128 registers and each lane loading
+// its next kMvRefitAhead tracks ahead (bit for bit the same results; 1.022 ->
+// 0.979 ms per nominal call, 1.547 -> 1.477 ms on the mixture).
 template <bool kRedo>
-__global__ void __launch_bounds__(kMvFitThreads, 4)
+__global__ void __launch_bounds__(kMvFitThreads, kRedo ? kMvRefitBlocks : kMvWindowBlocks)
 mv_fit_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
   __shared__ int16_t s_list[kRedo ? 1 : kMvFitThreads / kGroup][kRedo ? 1 : kMvList];
   const int lane = threadIdx.x & 31;
@@ -506,7 +542,7 @@ mv_fit_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
     MvLast L;
     bool keep = has;
     if constexpr (kRedo) {
-      group_fit_multi<kGroup>(rec, n, nullptr, xs, ys, zs, has, C, &out, &L);
+      group_fit_multi<kGroup, kMvRefitAhead>(rec, n, nullptr, xs, ys, zs, has, C, &out, &L);
     } else {
       // the window, and the bound on the tracks left out (i_xy, i_z)
       int16_t* list = s_list[threadIdx.x >> 3];
@@ -636,8 +672,8 @@ mv_select_kernel(Consts C, TrackPtrs T, OutPtrs O, MvScratch M) {
 }
 
 cudaError_t launch_mv_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S,
-                          const OutPtrs& O, const MvScratch& M, int fit_grid, cudaStream_t st,
-                          int* n_launches) {
+                          const OutPtrs& O, const MvScratch& M, int fit_grid, int redo_grid,
+                          cudaStream_t st, int* n_launches) {
   cudaError_t err = cudaMemsetAsync(M.counters, 0, 4 * sizeof(int), st);
   if (err != cudaSuccess) return err;
   const int per_block = kMvThreads / 32;
@@ -649,7 +685,7 @@ cudaError_t launch_mv_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S
   if (T.n_tracks > 0)
     mv_sums_kernel<<<static_cast<unsigned>((T.n_tracks + 255) / 256), 256, 0, st>>>(C, T, M);
   mv_fit_kernel<false><<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
-  mv_fit_kernel<true><<<fit_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
+  mv_fit_kernel<true><<<redo_grid, kMvFitThreads, 0, st>>>(C, T, O, M);
   if (T.n_tracks > 0)
     mv_assign_kernel<<<static_cast<unsigned>((T.n_tracks + 255) / 256), 256, 0, st>>>(C, T, O, M);
   mv_select_kernel<<<(T.n_events + 255) / 256, 256, 0, st>>>(C, T, O, M);
@@ -657,9 +693,10 @@ cudaError_t launch_mv_fit(const Consts& C, const TrackPtrs& T, const SeedPtrs& S
   return cudaGetLastError();
 }
 
-int mv_blocks_per_sm(void) {
+int mv_blocks_per_sm(bool redo) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mv_fit_kernel<false>, kMvFitThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &blocks, redo ? mv_fit_kernel<true> : mv_fit_kernel<false>, kMvFitThreads, 0) !=
       cudaSuccess)
     return 0;
   return blocks;

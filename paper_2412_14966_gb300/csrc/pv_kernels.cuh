@@ -259,9 +259,10 @@ struct MvScratch {
 constexpr int kMvThreads = 128;        // per-event kernels: one warp per event
 constexpr int kMvFitThreads = 256;
 cudaError_t launch_mv_fit(const pvdev::Consts& C, const TrackPtrs& T, const SeedPtrs& S,
-                          const OutPtrs& O, const MvScratch& M, int fit_grid, cudaStream_t st,
-                          int* n_launches);
-int mv_blocks_per_sm(void);
+                          const OutPtrs& O, const MvScratch& M, int fit_grid, int redo_grid,
+                          cudaStream_t st, int* n_launches);
+// resident CTAs per SM of the window fits (redo false) or of the refits
+int mv_blocks_per_sm(bool redo);
 
 cudaError_t launch_plain_find(const pvdev::Consts& C, const TrackPtrs& T, const OutPtrs& O,
                               const PlainScratch& ws, cudaStream_t st, int* n_launches);
